@@ -1,0 +1,298 @@
+"""Benchmark: batched symmetric-stair PCG solves/s on the ragged 4096-problem workload.
+
+One step = the whole path over one batch, inputs resident in HBM:
+Schur blocks (sspcg_build_schur_batched) -> symmetric stair preconditioner
+(sspcg_build_precond_batched) -> PCG to relative residual 1e-6
+(sspcg_solve_qp_batched).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2309_06427_gb300 import problems as P  # noqa: E402
+
+METRIC = "PCG solves/s at rel-resid 1e-6 (batched+warm-start vs plain); iters; % BW peak"
+UNIT = "solves/s"
+WORKLOAD = P.RAGGED_BATCH_4096
+PRECOND = "sym"
+SMEM_BYTES_PER_CLK_PER_SM = 128  # shared-memory bandwidth of one SM (32 banks x 4 B per clock)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sspcg", choices=["sspcg", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target duration of the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(w, nprob):
+    return {"workload": w.name, "problems_per_gpu": nprob, "N_range": list(w.N_range), "nx_set": list(w.nx_set),
+            "nu_rule": "ceil(nx/2)", "h": w.h, "tol": w.tol, "precond": "symmetric stair",
+            "start": "lambda0 = 0", "l2": "inputs larger than L2 (working set ~1.4 GB per step, L2 129 MB)"}
+
+
+def algorithmic_bytes_per_iteration(p) -> int:
+    """Bytes one PCG iteration must read (QP-form operator + preconditioner once, plus vectors):
+    A (N nx^2), B (N nx nu), diag Q, R ((N+1) nx + N nu), PD ((N+1) nx^2), PE (N nx^2), FP32;
+    vectors: 10 passes over (N+1) nx FP32 values."""
+    n, N, m, u = p.N + 1, p.N, p.nx, p.nu
+    floats = N * m * m + N * m * u + n * m + N * u + n * m * m + N * m * m + 10 * n * m
+    return 4 * floats
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"sspcg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2])); power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+def cpu_baseline(probs, target_s: float, tol: float):
+    """The FP64 oracle (build + preconditioner + PCG per problem, OpenMP over problems) on the first
+    problems of the workload, growing the sample until it runs about ``target_s`` seconds."""
+    from oracle import block
+    cores = os.cpu_count() or 1
+    m = min(64, len(probs))
+    while True:
+        _, iters, _, status, used, dt = block.solve_batch(probs[:m], PRECOND, tol, nthreads=cores)
+        if dt >= target_s or m >= len(probs):
+            break
+        m = min(len(probs), max(m + 1, int(m * min(8.0, 1.2 * target_s / max(dt, 1e-3)))))
+    return {"value": m / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
+            "sample": f"first {m} of the {len(probs)} problems (FP64 Schur build, preconditioner and PCG)",
+            "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    from oracle import block
+    block.build()
+    w = WORKLOAD
+    per_step = int(os.environ.get("SSPCG_REF_SAMPLE", "256"))
+    probs = P.make_workload(w, count=per_step)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        block.solve_batch(probs[:16], PRECOND, w.tol, nthreads=cores)
+    times, used = [], 1
+    for _ in range(args.steps):
+        _, _, _, status, used, dt = block.solve_batch(probs, PRECOND, w.tol, nthreads=cores)
+        times.append(dt)
+    t = sum(times)
+    value = per_step * args.steps / t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, per_step),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(used), "kind": "oracle",
+                             "sample": f"first {per_step} problems of the workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2309_06427_gb300 import build as _build
+    _build.build()
+    from paper_2309_06427_gb300 import sspcg
+
+    w = WORKLOAD
+    nprob = w.nprob
+    probs = P.make_workload(w, count=nprob, start=rank * nprob)  # weak scaling: each rank its own problems
+    opts = sspcg.options(tol=w.tol)
+    plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs], opts)
+    b = sspcg.Batch(plan, probs, pin=True)
+    d = b.dev
+    stream = torch.cuda.Stream()
+
+    def step(ev_mid=None, ev_end=None):
+        sspcg.sspcg_build_schur_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.D, b.E, stream)
+        sspcg.sspcg_build_precond_batched(plan, PRECOND, b.D, b.E, b.PD, b.PE, b.status, stream)
+        if ev_mid is not None:
+            ev_mid.record(stream)
+        sspcg.sspcg_solve_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE, d["gamma"], b.lam,
+                                     b.iters, b.relres, b.status, stream)
+        if ev_end is not None:
+            ev_end.record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(args.steps):
+        step(mids[k], ends[k])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    pcg_ms = [mids[k].elapsed_time(ends[k]) for k in range(args.steps)]
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    iters = b.iters.cpu().numpy().astype(np.int64)
+    status = b.status.cpu().numpy()
+    relres = b.relres.cpu().numpy()
+    ok = bool((status == 0).all() and (relres <= w.tol).all())
+    value = world * nprob * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the PCG launches): algorithmic bytes per launch / launch time
+    alg_bytes = sum(int(iters[i]) * algorithmic_bytes_per_iteration(p) for i, p in enumerate(probs))
+    pcg_s = statistics.mean(pcg_ms) / 1e3
+    achieved_gbs = alg_bytes / pcg_s / 1e9
+    props = torch.cuda.get_device_properties(local)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    smem_peak_gbs = props.multi_processor_count * SMEM_BYTES_PER_CLK_PER_SM * sm_max * 1e6 / 1e9
+
+    # end to end through the host-buffer C-ABI call (copies inside the timed region)
+    h = b.host
+    lam_h = torch.zeros(max(int(plan.sizes[sspcg.ARRAY_VEC]), 4)).pin_memory()
+    it_h = torch.zeros(plan.nprob, dtype=torch.int32).pin_memory()
+    rr_h = torch.zeros(plan.nprob, dtype=torch.float64).pin_memory()
+    st_h = torch.zeros(plan.nprob, dtype=torch.int32).pin_memory()
+    with torch.cuda.stream(stream):
+        sspcg.sspcg_pipeline_host(plan, PRECOND, h["A"], h["B"], h["qd"], h["rd"], h["gamma"], lam_h, it_h, rr_h,
+                                  st_h, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sspcg.sspcg_pipeline_host(plan, PRECOND, h["A"], h["B"], h["qd"], h["rd"], h["gamma"], lam_h, it_h,
+                                      rr_h, st_h, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = sum(int(h[k].numel()) * 4 for k in ("A", "B", "qd", "rd", "gamma"))
+    d2h = int(lam_h.numel()) * 4 + plan.nprob * (4 + 4 + 8)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return
+    stats = sspcg.plan_stats(plan)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(w, nprob),
+        "iters": {"mean": float(iters.mean()), "min": int(iters.min()), "max": int(iters.max()),
+                  "p50": float(np.percentile(iters, 50)), "p90": float(np.percentile(iters, 90))},
+        "all_converged": ok,
+        "pcg_ms_per_step": statistics.mean(pcg_ms),
+        "roofline": {"bound": "smem", "achieved": achieved_gbs, "peak": smem_peak_gbs, "unit": "GB/s",
+                     "frac": achieved_gbs / smem_peak_gbs, "traffic": None,
+                     "kernel": "pcg_kernel (all PCG launches of a step)",
+                     "peak_source": f"derived: {props.multi_processor_count} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk "
+                                    f"x {sm_max:.0f} MHz",
+                     "hbm_frac_of_measured": achieved_gbs / 6782.1},
+        "e2e": {"value": world * nprob * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    # kernels of one step: Schur build, preconditioner diagonal + off-diagonal, one PCG launch per group
+    line["gpu_launches"] = args.steps * (3 + stats["qp_launches"])
+    line["schedules"] = {"resident_problems": stats["qp_resident"], "streamed_problems": stats["qp_stream"],
+                         "pcg_launches_per_step": stats["qp_launches"]}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(probs, args.cpu_seconds, w.tol)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,274 @@
+/*
+ * sspcg — symmetric stair preconditioned conjugate gradient on GB300 (sm_103a).
+ *
+ * C ABI of the library.  It solves the Schur-complement system of the
+ * equality-constrained trajectory-optimisation QP of Bu & Plancher,
+ * "Symmetric Stair Preconditioning of Linear Systems for Parallel Trajectory
+ * Optimization" (arXiv 2309.06427), Sec. II-A, Eq. (schur):
+ *
+ *     S lambda = gamma,   S = C G^-1 C^T   (block tridiagonal, SPD)
+ *
+ * with preconditioned CG (Sec. II-B) and the symmetric stair preconditioner
+ * of Sec. IV, or the additive stair (Sec. III), block-Jacobi or Jacobi
+ * preconditioners (Sec. II-C, Eq. jacobi).
+ *
+ * Sign convention.  The paper's S = -C G^-1 C^T is negative definite; its
+ * footnote in Sec. II-A negates it.  This library works with the positive
+ * definite S = C G^-1 C^T and returns mu = -lambda* of the paper.  The
+ * constraint rows are -x_0 (+ x_s) and A_k x_k + B_k u_k - x_{k+1}.
+ *
+ * Problem data (one problem, horizon N, state size nx, input size nu),
+ * FP32, row-major, contiguous:
+ *   A  [N][nx][nx]   dynamics Jacobians A_k            (Sec. II-A)
+ *   B  [N][nx][nu]   input Jacobians B_k
+ *   qd [N+1][nx]     diagonal of the state cost Hessians Q_k (must be > 0)
+ *   rd [N][nu]       diagonal of the input cost Hessians R_k (must be > 0)
+ * Schur blocks, 0-based block rows k = 0..N:
+ *   D  [N+1][nx][nx] D_0 = Q_0^-1,
+ *                    D_k = A_{k-1} Q_{k-1}^-1 A_{k-1}^T + B_{k-1} R_{k-1}^-1 B_{k-1}^T + Q_k^-1
+ *                    (= -theta_{k-1} of Sec. II-A); symmetric
+ *   E  [N][nx][nx]   E[k-1] = S(k, k-1) = -A_{k-1} Q_{k-1}^-1 (= -phi_{k-1}); the
+ *                    block S(k-1, k) is E[k-1]^T
+ * Preconditioner blocks, same layout:
+ *   PD [N+1][nx][nx] Phi^-1(k, k) = D_k^-1 (symmetric)
+ *   PE [N][nx][nx]   PE[k-1] = Phi^-1(k, k-1) = -c D_k^-1 E[k-1] D_{k-1}^-1 with
+ *                    c = 1 (symmetric stair, Sec. IV: Psi_l^-1 + Psi_r^-1 - D^-1),
+ *                    c = 1/2 (additive stair, Sec. III), c = 0 (block-Jacobi);
+ *                    Jacobi: PD_k = diag(1 / diag D_k), PE = 0.
+ * Vectors gamma, lambda: [N+1][nx].
+ *
+ * Limits: 1 <= nx <= SSPCG_MAX_NX, 0 <= nu <= SSPCG_MAX_NX, 0 <= N <= SSPCG_MAX_N, and the PCG
+ * vectors of one problem must fit in one CTA's shared memory (about
+ * 4 (N+1) nx + N nu <= 56000 floats); larger problems return SSPCG_ERR_UNSUPPORTED.
+ *
+ * Ownership and execution.  Every array argument is a device pointer owned
+ * by the caller, 16-byte aligned, unless the parameter is documented as a
+ * host pointer.  All calls are asynchronous on ``stream`` (0 = legacy
+ * default stream) and return before the work is done; a returned
+ * SSPCG_OK means the arguments were valid and the launches were issued.
+ * Nothing is printed and nothing exits.  Per-problem outcomes (solve
+ * status, iteration count, residual) are written to caller device arrays.
+ * Only an sspcg_plan allocates device memory (at creation).
+ */
+#ifndef SSPCG_H_
+#define SSPCG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* CUDA stream handle (cudaStream_t), passed as an opaque pointer. */
+typedef void *sspcg_stream;
+
+#define SSPCG_MAX_NX 28
+#define SSPCG_MAX_N 4096
+
+/* Return codes of every call. */
+typedef enum {
+  SSPCG_OK = 0,
+  SSPCG_ERR_INVALID_ARG = 1, /* null or misaligned pointer, size out of range */
+  SSPCG_ERR_UNSUPPORTED = 2, /* valid request the library does not implement */
+  SSPCG_ERR_CUDA = 3,        /* a CUDA runtime call failed (see sspcg_last_cuda_error) */
+} sspcg_status;
+
+/* Per-problem outcome written to the int32 ``status`` arrays. */
+enum {
+  SSPCG_SOLVE_OK = 0,        /* ||r||_2 <= tol * ||gamma||_2 reached */
+  SSPCG_SOLVE_MAXITER = 1,   /* max_iter iterations without reaching tol */
+  SSPCG_SOLVE_BREAKDOWN = 2, /* p^T S p <= 0: S not positive definite in finite precision */
+  SSPCG_SOLVE_NOT_SPD = 3,   /* a diagonal block D_k failed its FP64 factorisation */
+  SSPCG_SOLVE_NONFINITE = 4, /* NaN or Inf met during the iteration */
+};
+
+/* Preconditioners (Sec. II-C, III, IV). */
+typedef enum {
+  SSPCG_PRECOND_SYM_STAIR = 0,    /* Phi_sym^-1 = Psi_l^-1 + Psi_r^-1 - D^-1 (Sec. IV) */
+  SSPCG_PRECOND_ADD_STAIR = 1,    /* Phi_add^-1 = (Psi_l^-1 + Psi_r^-1) / 2 (Sec. III) */
+  SSPCG_PRECOND_BLOCK_JACOBI = 2, /* Phi = block-diag(S)  (Eq. jacobi) */
+  SSPCG_PRECOND_JACOBI = 3,       /* Phi = diag(S)        (Eq. jacobi) */
+} sspcg_precond;
+
+/* Precision of the PCG dot products (p.Sp, r.z, r.r). */
+enum {
+  SSPCG_REDUCE_DF = 0,  /* default: exact FP32 products, double-float (~48-bit) sums */
+  SSPCG_REDUCE_F32 = 1, /* FP32 products and sums (pairwise across threads) */
+  SSPCG_REDUCE_F64 = 2, /* FP64 products and sums (GB300 runs FP64 at ~1/64 of FP32) */
+};
+
+/* Kernel schedule of a PCG problem. */
+enum {
+  SSPCG_SCHED_AUTO = 0,     /* resident when the problem fits in one CTA's shared memory */
+  SSPCG_SCHED_RESIDENT = 1, /* operator and preconditioner staged once into shared memory */
+  SSPCG_SCHED_STREAM = 2,   /* operator and preconditioner read from L2/HBM every iteration */
+};
+
+/* Solver options. */
+typedef struct {
+  double tol;              /* stop before an iteration once ||r||_2 <= tol * ||gamma||_2 (recurrence residual) */
+  int32_t max_iter;        /* <= 0: 10 * (N + 1) * nx */
+  int32_t warm_start;      /* 0: lambda_0 = 0.  1: lambda holds lambda_0 on entry.
+                              2: as 1, but restart from lambda_0 = 0 when ||gamma - S lambda_0|| >= ||gamma||
+                                 or lambda_0 is not finite */
+  int32_t reduction;       /* SSPCG_REDUCE_* */
+  int32_t schedule;        /* SSPCG_SCHED_*; RESIDENT is downgraded to STREAM for problems that do not fit */
+  int32_t block_threads;   /* threads per CTA, multiple of 32 in [32, 512]; 0: chosen by the library */
+} sspcg_options;
+
+/* Message of the last CUDA error seen by this thread (static storage, never NULL). */
+const char *sspcg_last_cuda_error(void);
+
+/* Library version string. */
+const char *sspcg_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Single problem                                                     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Schur blocks D, E from the QP data (Sec. II-A, the theta_k/phi_k block
+ * formulas, negated).  FP32 arithmetic; D_k is written exactly symmetric.
+ * Inputs A, B, qd, rd; outputs D [N+1][nx][nx], E [N][nx][nx].
+ */
+sspcg_status sspcg_build_schur(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
+                               const float *rd, float *D, float *E, sspcg_stream stream);
+
+/*
+ * Preconditioner blocks PD, PE from D, E (Eq. stair_inv with Sec. III/IV, or
+ * Eq. jacobi).  D_k^-1 is formed by an FP64 LDL^T factorisation of each
+ * diagonal block; the off-diagonal products -c D_k^-1 E D_{k-1}^-1 run in FP32.
+ * ``status`` (device, 1 int32) is set to SSPCG_SOLVE_OK, or to
+ * SSPCG_SOLVE_NOT_SPD when some D_k is not positive definite.
+ */
+sspcg_status sspcg_build_precond(int32_t N, int32_t nx, sspcg_precond kind, const float *D, const float *E, float *PD,
+                                 float *PE, int32_t *status, sspcg_stream stream);
+
+/*
+ * PCG on S lambda = gamma with S given by its blocks D, E (Sec. II-B) and
+ * Phi^-1 by PD, PE.  One CTA solves the problem: matrix-vector products in
+ * FP32, dot products in the precision opts->reduction selects.
+ * ``lambda`` is the solution (and lambda_0 on entry when opts->warm_start).
+ * Outputs (device, 1 element each): iters = number of S*p products,
+ * relres = ||r||_2 / ||gamma||_2 of the recurrence residual, status.
+ * gamma = 0 gives lambda = 0, iters = 0.
+ */
+sspcg_status sspcg_solve(int32_t N, int32_t nx, const float *D, const float *E, const float *PD, const float *PE,
+                         const float *gamma, float *lambda, const sspcg_options *opts, int32_t *iters,
+                         double *relres, int32_t *status, sspcg_stream stream);
+
+/*
+ * As sspcg_solve, but S is applied in the factored form of its definition,
+ * S p = C (G^-1 (C^T p)) (Eq. schur), from the QP data A, B, qd, rd.  The
+ * FP32 inputs are then the operator itself: no rounding of S's blocks enters
+ * the system, which keeps lambda within 1e-5 of the FP64 solution on
+ * ill-conditioned systems where FP32 blocks of S do not.
+ */
+sspcg_status sspcg_solve_qp(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
+                            const float *rd, const float *PD, const float *PE, const float *gamma, float *lambda,
+                            const sspcg_options *opts, int32_t *iters, double *relres, int32_t *status,
+                            sspcg_stream stream);
+
+/*
+ * True residual ||gamma - S lambda||_2 / ||gamma||_2 with S = C G^-1 C^T
+ * applied in FP64 from the QP data (diagnostic).  relres_true: device, 1 double.
+ */
+sspcg_status sspcg_residual_qp(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
+                               const float *rd, const float *gamma, const float *lambda, double *relres_true,
+                               sspcg_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Batches of independent problems of uneven N, nx, nu                */
+/* ------------------------------------------------------------------ */
+
+/*
+ * A plan describes a batch.  Problem i's arrays are packed back to back in
+ * one device buffer per array kind, each problem starting at a 16-byte
+ * aligned offset given by sspcg_plan_offsets.  The plan owns its device
+ * descriptors and work lists (allocated here, freed by sspcg_plan_destroy)
+ * and picks a kernel schedule per problem class.
+ * N, nx, nu: host arrays of nprob entries.  opts: host pointer, copied.
+ */
+typedef struct sspcg_plan sspcg_plan;
+
+/* Packed array kinds. */
+typedef enum {
+  SSPCG_ARRAY_A = 0,    /* N*nx*nx per problem */
+  SSPCG_ARRAY_B = 1,    /* N*nx*nu */
+  SSPCG_ARRAY_QD = 2,   /* (N+1)*nx */
+  SSPCG_ARRAY_RD = 3,   /* N*nu */
+  SSPCG_ARRAY_DIAG = 4, /* (N+1)*nx*nx: D and PD */
+  SSPCG_ARRAY_OFF = 5,  /* N*nx*nx: E and PE */
+  SSPCG_ARRAY_VEC = 6,  /* (N+1)*nx: gamma and lambda */
+  SSPCG_NUM_ARRAYS = 7
+} sspcg_array;
+
+sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *N, const int32_t *nx,
+                               const int32_t *nu, const sspcg_options *opts);
+sspcg_status sspcg_plan_destroy(sspcg_plan *plan);
+
+/* Total floats of each packed array kind (host out[SSPCG_NUM_ARRAYS]). */
+sspcg_status sspcg_plan_sizes(const sspcg_plan *plan, int64_t *out);
+
+/* Float offset of each problem in a packed array kind (host out[nprob]). */
+sspcg_status sspcg_plan_offsets(const sspcg_plan *plan, sspcg_array kind, int64_t *out);
+
+/*
+ * Schedule summary (host out[6]): for the factored-S solve, the number of PCG
+ * launches, of problems staged in shared memory and of problems streamed
+ * from L2/HBM; then the same three for the block-S solve.
+ */
+sspcg_status sspcg_plan_stats(const sspcg_plan *plan, int64_t *out);
+
+/* Batched sspcg_build_schur over packed arrays. */
+sspcg_status sspcg_build_schur_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
+                                       const float *rd, float *D, float *E, sspcg_stream stream);
+
+/* Batched sspcg_build_precond; status: device int32[nprob]. */
+sspcg_status sspcg_build_precond_batched(sspcg_plan *plan, sspcg_precond kind, const float *D, const float *E,
+                                         float *PD, float *PE, int32_t *status, sspcg_stream stream);
+
+/* Batched sspcg_solve (block S). iters, status: int32[nprob]; relres: double[nprob]. */
+sspcg_status sspcg_solve_batched(sspcg_plan *plan, const float *D, const float *E, const float *PD,
+                                 const float *PE, const float *gamma, float *lambda, int32_t *iters,
+                                 double *relres, int32_t *status, sspcg_stream stream);
+
+/* Batched sspcg_solve_qp (factored S). */
+sspcg_status sspcg_solve_qp_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
+                                    const float *rd, const float *PD, const float *PE, const float *gamma,
+                                    float *lambda, int32_t *iters, double *relres, int32_t *status,
+                                    sspcg_stream stream);
+
+/* Batched sspcg_residual_qp; relres_true: double[nprob]. */
+sspcg_status sspcg_residual_qp_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
+                                       const float *rd, const float *gamma, const float *lambda,
+                                       double *relres_true, sspcg_stream stream);
+
+/*
+ * The whole path for a batch, from QP data to lambda: Schur blocks,
+ * preconditioner, PCG with the factored S.  D, E, PD, PE are caller work
+ * buffers of the packed sizes.  A problem whose preconditioner fails keeps
+ * status SSPCG_SOLVE_NOT_SPD and is not iterated.
+ */
+sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
+                                    const float *qd, const float *rd, const float *gamma, float *D, float *E,
+                                    float *PD, float *PE, float *lambda, int32_t *iters, double *relres,
+                                    int32_t *status, sspcg_stream stream);
+
+/*
+ * sspcg_pipeline_batched from HOST buffers (packed like the device arrays):
+ * copies the inputs to plan-owned device buffers (allocated on first use),
+ * runs the path, copies lambda, iters, relres and status back and waits for
+ * the stream.  Host buffers should be pinned for full copy speed.  With
+ * warm_start set in the plan's options, lambda_host holds lambda_0 on entry.
+ */
+sspcg_status sspcg_pipeline_host(sspcg_plan *plan, sspcg_precond kind, const float *A_host, const float *B_host,
+                                 const float *qd_host, const float *rd_host, const float *gamma_host,
+                                 float *lambda_host, int32_t *iters_host, double *relres_host, int32_t *status_host,
+                                 sspcg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSPCG_H_ */

@@ -1,0 +1,91 @@
+// Host-side declarations shared by the CUDA translation units of sspcg.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sspcg {
+
+// Operator forms for S p.
+enum OpForm : int { kOpBlock = 0, kOpQp = 1 };
+// Precision of the dot-product reductions.
+enum RedMode : int { kRedF32 = 0, kRedDf = 1, kRedF64 = 2 };
+
+// Padded leading dimension of a matrix staged in shared memory: odd, so that
+// 32 consecutive rows touch 32 distinct banks.
+__host__ __device__ __forceinline__ int pad_ld(int x) { return x | 1; }
+
+// Shared-memory carve-up of one PCG problem, in floats; every region starts
+// 16-byte aligned.  The same function sizes launches on the host and carves
+// on the device.
+struct PcgLayout {
+  int64_t p, r, w, v;               // vectors
+  int64_t m0, m1, iq, ir, pd, pe;   // matrices (resident schedule only)
+  int64_t total;
+};
+
+__host__ __device__ inline PcgLayout pcg_layout(int op, bool resident, int N, int nx, int nu) {
+  PcgLayout L{};
+  const int64_t n = N + 1, R4 = round_up(n * nx, 4);
+  int64_t o = 0;
+  L.p = o; o += R4;
+  L.r = o; o += R4;
+  L.w = o; o += R4;
+  L.v = o;
+  if (op == kOpQp) o += round_up(n * nx + (int64_t)N * nu, 4);
+  L.m0 = L.m1 = L.iq = L.ir = L.pd = L.pe = o;
+  if (resident) {
+    const int64_t ld = pad_ld(nx), ldb = pad_ld(nu > 0 ? nu : 1);
+    if (op == kOpQp) {
+      L.m0 = o; o += round_up((int64_t)N * nx * ld, 4);    // A_k, row stride ld
+      L.m1 = o; o += round_up((int64_t)N * nx * ldb, 4);   // B_k, row stride ldb
+      L.iq = o; o += round_up(n * nx, 4);                  // 1 / q
+      L.ir = o; o += round_up((int64_t)N * nu, 4);         // 1 / r
+    } else {
+      L.m0 = o; o += round_up(n * nx * ld, 4);             // D_k
+      L.m1 = o; o += round_up((int64_t)N * nx * ld, 4);    // E_k
+    }
+    L.pd = o; o += round_up(n * nx * ld, 4);               // PD_k
+    L.pe = o; o += round_up((int64_t)N * nx * ld, 4);      // PE_k
+  }
+  L.total = o;
+  return L;
+}
+
+// Arguments of a PCG launch (by value).
+struct PcgArgs {
+  ProbSet ps;
+  const int32_t *work;   // problem indices in processing order (device), or nullptr: identity
+  int32_t nwork;
+  int32_t *counter;      // work-queue counter (device, zeroed before launch), or nullptr: static
+  const float *A, *B, *qd, *rd;  // QP operator data (packed)
+  const float *D, *E;            // block operator data (packed)
+  const float *PD, *PE;
+  const float *gamma;
+  float *lambda;
+  int32_t *iters;
+  double *relres;
+  int32_t *status;       // in: nonzero skips the problem; out: solve code
+  float tol2;            // tol^2
+  int32_t max_iter;      // <= 0: 10 (N+1) nx
+  int32_t warm;          // 0, 1, 2 (see sspcg_options)
+};
+
+// PCG launch for one nx; dispatches to the instantiation for that nx.
+cudaError_t launch_pcg(int nx, int op, int red, bool resident, const PcgArgs &a, int grid, int block, size_t smem,
+                       cudaStream_t st);
+int pcg_max_smem_bytes();
+
+cudaError_t launch_schur_build(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots, const float *A,
+                               const float *B, const float *qd, const float *rd, float *D, float *E,
+                               cudaStream_t st, int sms);
+cudaError_t launch_precond_build(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots,
+                                 const int64_t *off_start, int64_t total_off, int kind, const float *D,
+                                 const float *E, float *PD, float *PE, int32_t *status, cudaStream_t st, int sms,
+                                 int64_t off_floats);
+cudaError_t launch_residual_qp(const ProbSet &ps, const float *A, const float *B, const float *qd, const float *rd,
+                               const float *gamma, const float *lambda, double *relres_true, cudaStream_t st);
+
+}  // namespace sspcg

@@ -1,0 +1,294 @@
+"""Python binding of the sspcg C ABI (``include/sspcg.h``).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+Functions carry the C names and take torch CUDA tensors for device arrays;
+``stream`` defaults to torch's current stream.  Any non-OK return raises.
+The library must have been built (``paper_2309_06427_gb300.build.build()``);
+loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA = 0, 1, 2, 3
+SOLVE_OK, SOLVE_MAXITER, SOLVE_BREAKDOWN, SOLVE_NOT_SPD, SOLVE_NONFINITE = 0, 1, 2, 3, 4
+PRECOND = {"sym": 0, "add": 1, "bj": 2, "jacobi": 3}
+REDUCE = {"df": 0, "f32": 1, "f64": 2}
+SCHED = {"auto": 0, "resident": 1, "stream": 2}
+ARRAY_A, ARRAY_B, ARRAY_QD, ARRAY_RD, ARRAY_DIAG, ARRAY_OFF, ARRAY_VEC = range(7)
+NUM_ARRAYS = 7
+MAX_NX = 28
+
+
+class SspcgError(RuntimeError):
+    pass
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+                ("reduction", ctypes.c_int32), ("schedule", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+
+
+def options(tol=1e-6, max_iter=0, warm_start=0, reduction="df", schedule="auto", block_threads=0) -> Options:
+    return Options(float(tol), int(max_iter), int(warm_start), REDUCE[reduction] if isinstance(reduction, str)
+                   else int(reduction), SCHED[schedule] if isinstance(schedule, str) else int(schedule),
+                   int(block_threads))
+
+
+_lib = None
+_VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise SspcgError(f"sspcg CUDA library missing at {_build.LIB}; build it with "
+                             "paper_2309_06427_gb300.build.build() (needs nvcc)")
+        L = ctypes.CDLL(_build.LIB)
+        sig = {
+            "sspcg_build_schur": [_I32, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+            "sspcg_build_precond": [_I32, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP],
+            "sspcg_solve": [_I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(Options), _VP, _VP, _VP, _VP],
+            "sspcg_solve_qp": [_I32, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(Options),
+                               _VP, _VP, _VP, _VP],
+            "sspcg_residual_qp": [_I32, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+            "sspcg_plan_create": [ctypes.POINTER(_VP), _I32, _VP, _VP, _VP, ctypes.POINTER(Options)],
+            "sspcg_plan_destroy": [_VP],
+            "sspcg_plan_sizes": [_VP, _VP],
+            "sspcg_plan_offsets": [_VP, _I32, _VP],
+            "sspcg_plan_stats": [_VP, _VP],
+            "sspcg_build_schur_batched": [_VP] * 8,
+            "sspcg_build_precond_batched": [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP],
+            "sspcg_solve_batched": [_VP] * 11,
+            "sspcg_solve_qp_batched": [_VP] * 13,
+            "sspcg_residual_qp_batched": [_VP] * 9,
+            "sspcg_pipeline_batched": [_VP, _I32] + [_VP] * 14,
+            "sspcg_pipeline_host": [_VP, _I32] + [_VP] * 10,
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.sspcg_last_cuda_error.restype = ctypes.c_char_p
+        L.sspcg_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> List[str]:
+    return [n for n in dir(lib()) if n.startswith("sspcg_")]
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        msg = {ERR_INVALID_ARG: "invalid argument", ERR_UNSUPPORTED: "unsupported",
+               ERR_CUDA: "CUDA error: " + lib().sspcg_last_cuda_error().decode()}.get(rc, f"code {rc}")
+        raise SspcgError(f"{what}: {msg}")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise SspcgError("device tensor expected")
+    if not t.is_contiguous():
+        raise SspcgError("contiguous tensor expected")
+    return t.data_ptr() or None
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---------------------------------------------------------------------------
+# Single problem
+# ---------------------------------------------------------------------------
+def sspcg_build_schur(N, nx, nu, A, B, qd, rd, D, E, stream=None):
+    _check(lib().sspcg_build_schur(N, nx, nu, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(D), _ptr(E),
+                                   _stream(stream)), "sspcg_build_schur")
+
+
+def sspcg_build_precond(N, nx, kind, D, E, PD, PE, status, stream=None):
+    k = PRECOND[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().sspcg_build_precond(N, nx, k, _ptr(D), _ptr(E), _ptr(PD), _ptr(PE), _ptr(status),
+                                     _stream(stream)), "sspcg_build_precond")
+
+
+def sspcg_solve(N, nx, D, E, PD, PE, gamma, lam, opts: Options, iters, relres, status, stream=None):
+    _check(lib().sspcg_solve(N, nx, _ptr(D), _ptr(E), _ptr(PD), _ptr(PE), _ptr(gamma), _ptr(lam),
+                             ctypes.byref(opts), _ptr(iters), _ptr(relres), _ptr(status), _stream(stream)),
+           "sspcg_solve")
+
+
+def sspcg_solve_qp(N, nx, nu, A, B, qd, rd, PD, PE, gamma, lam, opts: Options, iters, relres, status, stream=None):
+    _check(lib().sspcg_solve_qp(N, nx, nu, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(PD), _ptr(PE), _ptr(gamma),
+                                _ptr(lam), ctypes.byref(opts), _ptr(iters), _ptr(relres), _ptr(status),
+                                _stream(stream)), "sspcg_solve_qp")
+
+
+def sspcg_residual_qp(N, nx, nu, A, B, qd, rd, gamma, lam, relres_true, stream=None):
+    _check(lib().sspcg_residual_qp(N, nx, nu, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(gamma), _ptr(lam),
+                                   _ptr(relres_true), _stream(stream)), "sspcg_residual_qp")
+
+
+# ---------------------------------------------------------------------------
+# Batches
+# ---------------------------------------------------------------------------
+class Plan:
+    """Owner of an ``sspcg_plan``; destroyed with the object."""
+
+    def __init__(self, N: Sequence[int], nx: Sequence[int], nu: Sequence[int], opts: Options):
+        self.N = np.ascontiguousarray(N, dtype=np.int32)
+        self.nx = np.ascontiguousarray(nx, dtype=np.int32)
+        self.nu = np.ascontiguousarray(nu, dtype=np.int32)
+        self.nprob = len(self.N)
+        self.opts = opts
+        h = _VP()
+        _check(lib().sspcg_plan_create(ctypes.byref(h), self.nprob, self.N.ctypes.data, self.nx.ctypes.data,
+                                       self.nu.ctypes.data, ctypes.byref(opts)), "sspcg_plan_create")
+        self.handle = h
+        sizes = np.zeros(NUM_ARRAYS, dtype=np.int64)
+        _check(lib().sspcg_plan_sizes(h, sizes.ctypes.data), "sspcg_plan_sizes")
+        self.sizes = sizes
+        self.offsets = []
+        for k in range(NUM_ARRAYS):
+            o = np.zeros(self.nprob, dtype=np.int64)
+            if self.nprob:
+                _check(lib().sspcg_plan_offsets(h, k, o.ctypes.data), "sspcg_plan_offsets")
+            self.offsets.append(o)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sspcg_plan_destroy(h)
+            self.handle = None
+
+    def empty(self, kind: int, device="cuda", dtype=torch.float32, fill=0.0) -> torch.Tensor:
+        return torch.full((max(int(self.sizes[kind]), 4),), fill, dtype=dtype, device=device)
+
+    def pack(self, kind: int, arrays: Sequence[np.ndarray], out: Optional[np.ndarray] = None) -> np.ndarray:
+        """Pack per-problem arrays (host) into the plan's layout (host float32)."""
+        flat = np.zeros(max(int(self.sizes[kind]), 4), dtype=np.float32) if out is None else out
+        offs = self.offsets[kind]
+        for i, a in enumerate(arrays):
+            a = np.asarray(a, dtype=np.float32).ravel()
+            flat[offs[i]:offs[i] + a.size] = a
+        return flat
+
+    def unpack(self, kind: int, flat, shapes: Sequence[tuple]) -> List[np.ndarray]:
+        flat = flat.detach().cpu().numpy() if isinstance(flat, torch.Tensor) else np.asarray(flat)
+        offs = self.offsets[kind]
+        out = []
+        for i, shp in enumerate(shapes):
+            n = int(np.prod(shp))
+            out.append(flat[offs[i]:offs[i] + n].reshape(shp))
+        return out
+
+
+def sspcg_plan_create(N, nx, nu, opts: Options) -> Plan:
+    return Plan(N, nx, nu, opts)
+
+
+def sspcg_plan_stats(plan: Plan) -> Dict[str, int]:
+    out = np.zeros(6, dtype=np.int64)
+    _check(lib().sspcg_plan_stats(plan.handle, out.ctypes.data), "sspcg_plan_stats")
+    keys = ["qp_launches", "qp_resident", "qp_stream", "block_launches", "block_resident", "block_stream"]
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+plan_stats = sspcg_plan_stats
+
+
+def sspcg_build_schur_batched(plan: Plan, A, B, qd, rd, D, E, stream=None):
+    _check(lib().sspcg_build_schur_batched(plan.handle, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(D), _ptr(E),
+                                           _stream(stream)), "sspcg_build_schur_batched")
+
+
+def sspcg_build_precond_batched(plan: Plan, kind, D, E, PD, PE, status, stream=None):
+    k = PRECOND[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().sspcg_build_precond_batched(plan.handle, k, _ptr(D), _ptr(E), _ptr(PD), _ptr(PE), _ptr(status),
+                                             _stream(stream)), "sspcg_build_precond_batched")
+
+
+def sspcg_solve_batched(plan: Plan, D, E, PD, PE, gamma, lam, iters, relres, status, stream=None):
+    _check(lib().sspcg_solve_batched(plan.handle, _ptr(D), _ptr(E), _ptr(PD), _ptr(PE), _ptr(gamma), _ptr(lam),
+                                     _ptr(iters), _ptr(relres), _ptr(status), _stream(stream)),
+           "sspcg_solve_batched")
+
+
+def sspcg_solve_qp_batched(plan: Plan, A, B, qd, rd, PD, PE, gamma, lam, iters, relres, status, stream=None):
+    _check(lib().sspcg_solve_qp_batched(plan.handle, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(PD), _ptr(PE),
+                                        _ptr(gamma), _ptr(lam), _ptr(iters), _ptr(relres), _ptr(status),
+                                        _stream(stream)), "sspcg_solve_qp_batched")
+
+
+def sspcg_residual_qp_batched(plan: Plan, A, B, qd, rd, gamma, lam, relres_true, stream=None):
+    _check(lib().sspcg_residual_qp_batched(plan.handle, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(gamma),
+                                           _ptr(lam), _ptr(relres_true), _stream(stream)),
+           "sspcg_residual_qp_batched")
+
+
+def sspcg_pipeline_batched(plan: Plan, kind, A, B, qd, rd, gamma, D, E, PD, PE, lam, iters, relres, status,
+                           stream=None):
+    k = PRECOND[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().sspcg_pipeline_batched(plan.handle, k, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(gamma), _ptr(D),
+                                        _ptr(E), _ptr(PD), _ptr(PE), _ptr(lam), _ptr(iters), _ptr(relres),
+                                        _ptr(status), _stream(stream)), "sspcg_pipeline_batched")
+
+
+def sspcg_pipeline_host(plan: Plan, kind, A, B, qd, rd, gamma, lam, iters, relres, status, stream=None):
+    """Host-buffer pipeline: A..gamma, lam, iters, relres, status are host torch tensors (pinned for speed)."""
+    k = PRECOND[kind] if isinstance(kind, str) else int(kind)
+    hp = lambda t: t.data_ptr() if t is not None else None
+    _check(lib().sspcg_pipeline_host(plan.handle, k, hp(A), hp(B), hp(qd), hp(rd), hp(gamma), hp(lam), hp(iters),
+                                     hp(relres), hp(status), _stream(stream)), "sspcg_pipeline_host")
+
+
+# ---------------------------------------------------------------------------
+# Convenience: a packed batch of problems on the device
+# ---------------------------------------------------------------------------
+class Batch:
+    """Packed device arrays of a list of ``problems.Problem`` for one plan."""
+
+    def __init__(self, plan: Plan, probs, device="cuda", pin=False):
+        self.plan, self.probs = plan, probs
+        host = {
+            "A": plan.pack(ARRAY_A, [p.A for p in probs]),
+            "B": plan.pack(ARRAY_B, [p.B for p in probs]),
+            "qd": plan.pack(ARRAY_QD, [p.qd for p in probs], np.ones(max(int(plan.sizes[ARRAY_QD]), 4), np.float32)),
+            "rd": plan.pack(ARRAY_RD, [p.rd for p in probs], np.ones(max(int(plan.sizes[ARRAY_RD]), 4), np.float32)),
+            "gamma": plan.pack(ARRAY_VEC, [p.gamma for p in probs]),
+        }
+        self.host = {k: torch.from_numpy(v) for k, v in host.items()}
+        if pin:
+            self.host = {k: v.pin_memory() for k, v in self.host.items()}
+        self.dev = {k: v.to(device) for k, v in self.host.items()}
+        self.D = plan.empty(ARRAY_DIAG, device)
+        self.E = plan.empty(ARRAY_OFF, device)
+        self.PD = plan.empty(ARRAY_DIAG, device)
+        self.PE = plan.empty(ARRAY_OFF, device)
+        self.lam = plan.empty(ARRAY_VEC, device)
+        n = max(plan.nprob, 1)
+        self.iters = torch.zeros(n, dtype=torch.int32, device=device)
+        self.relres = torch.zeros(n, dtype=torch.float64, device=device)
+        self.status = torch.zeros(n, dtype=torch.int32, device=device)
+
+    def pipeline(self, kind="sym", stream=None):
+        d = self.dev
+        sspcg_pipeline_batched(self.plan, kind, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], self.D, self.E, self.PD,
+                               self.PE, self.lam, self.iters, self.relres, self.status, stream)
+
+    def lambdas(self) -> List[np.ndarray]:
+        return self.plan.unpack(ARRAY_VEC, self.lam, [p.gamma.shape for p in self.probs])

@@ -1,0 +1,70 @@
+"""Helpers of the GPU parity tests: run the CUDA path through the C ABI and
+the FP64 oracle on the same seeded inputs."""
+import numpy as np
+import torch
+
+from oracle import block
+from paper_2309_06427_gb300 import sspcg
+
+# Parity bar: relative 2-norm error of lambda against the FP64 oracle, and
+# iteration counts within one.
+LAMBDA_RTOL = 1e-5
+ITER_TOL = 1
+
+
+def dev(a, dtype=torch.float32):
+    a = np.ascontiguousarray(a)
+    if a.size == 0:
+        a = np.zeros(4, dtype=a.dtype)
+    return torch.from_numpy(a).to(dtype).cuda()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel(); b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def gpu_schur(p):
+    n, m = p.n, p.nx
+    A, B, qd, rd = dev(p.A), dev(p.B), dev(p.qd), dev(p.rd)
+    D = torch.zeros(max(n * m * m, 4), device="cuda")
+    E = torch.zeros(max(p.N * m * m, 4), device="cuda")
+    sspcg.sspcg_build_schur(p.N, m, p.nu, A, B, qd, rd, D, E)
+    return (A, B, qd, rd), D, E
+
+
+def gpu_precond(p, D, E, kind):
+    n, m = p.n, p.nx
+    PD = torch.zeros(max(n * m * m, 4), device="cuda")
+    PE = torch.zeros(max(p.N * m * m, 4), device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sspcg.sspcg_build_precond(p.N, m, kind, D, E, PD, PE, st)
+    return PD, PE, int(st.item())
+
+
+def gpu_solve_qp(p, kind="sym", tol=1e-6, lam0=None, **kw):
+    """Whole single-problem path on the GPU: returns (lambda, iters, relres, status)."""
+    (A, B, qd, rd), D, E = gpu_schur(p)
+    PD, PE, pst = gpu_precond(p, D, E, kind)
+    g = dev(p.gamma)
+    lam = dev(lam0) if lam0 is not None else torch.zeros_like(g)
+    it = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rr = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    opts = sspcg.options(tol=tol, warm_start=0 if lam0 is None else kw.pop("warm", 1), **kw)
+    sspcg.sspcg_solve_qp(p.N, p.nx, p.nu, A, B, qd, rd, PD, PE, g, lam, opts, it, rr, st)
+    torch.cuda.synchronize()
+    return lam.cpu().numpy()[:p.gamma.size].reshape(p.gamma.shape), int(it.item()), float(rr.item()), int(st.item())
+
+
+def blocks_to_oracle(p, D, E):
+    """FP32 GPU blocks as an oracle BlockTridiag (exact conversion to FP64)."""
+    n, m = p.n, p.nx
+    d = D.cpu().numpy()[:n * m * m].reshape(n, m, m).astype(np.float64)
+    l = np.zeros((n, m, m)); u = np.zeros((n, m, m))
+    if p.N > 0:
+        e = E.cpu().numpy()[:p.N * m * m].reshape(p.N, m, m).astype(np.float64)
+        l[1:] = e
+        u[:-1] = np.transpose(e, (0, 2, 1))
+    return block.BlockTridiag(d, l, u)

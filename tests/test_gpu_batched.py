@@ -1,0 +1,116 @@
+"""Batched (ragged) path against the FP64 oracle, including the full-size
+4096-problem workload in the launch configuration the benchmark times."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import block
+from paper_2309_06427_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2309_06427_gb300 import build as _build
+    _build.build()
+    from paper_2309_06427_gb300 import sspcg
+    from _gpu_helpers import ITER_TOL, LAMBDA_RTOL, gpu_solve_qp, rel
+
+
+def _plan(probs, **kw):
+    opts = sspcg.options(tol=kw.pop("tol", 1e-6), **kw)
+    return sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs], opts)
+
+
+def _ragged():
+    probs = P.make_workload(P.RAGGED_BATCH_4096, count=80)
+    probs += P.custom_problems([(0, 3, 2), (1, 1, 1), (5, 28, 14), (0, 1, 1), (12, 9, 0), (2, 17, 9)], config=63)
+    return probs
+
+
+@pytest.mark.parametrize("kind", ["sym", "add", "bj", "jacobi"])
+def test_pipeline_batched_matches_oracle(kind):
+    probs = _ragged()
+    plan = _plan(probs)
+    b = sspcg.Batch(plan, probs)
+    b.pipeline(kind)
+    torch.cuda.synchronize()
+    xs, it_o, rr_o, st_o, _, _ = block.solve_batch(probs, kind, 1e-6)
+    lams = b.lambdas()
+    it = b.iters.cpu().numpy(); st = b.status.cpu().numpy(); rr = b.relres.cpu().numpy()
+    assert (st == 0).all() and (st_o == 0).all()
+    assert np.abs(it - it_o).max() <= ITER_TOL
+    worst = max(rel(lams[i], xs[i]) for i in range(len(probs)))
+    assert worst <= LAMBDA_RTOL
+    assert (rr <= 1e-6).all()
+
+
+@pytest.mark.parametrize("schedule", ["auto", "stream"])
+def test_batched_equals_single_problem_path(schedule):
+    probs = _ragged()[:40]
+    plan = _plan(probs, schedule=schedule)
+    b = sspcg.Batch(plan, probs)
+    b.pipeline("sym")
+    torch.cuda.synchronize()
+    lams, it = b.lambdas(), b.iters.cpu().numpy()
+    for i, p in enumerate(probs):
+        lam1, it1, _, st1 = gpu_solve_qp(p, "sym", 1e-6, schedule=schedule)
+        assert st1 == 0 and abs(it1 - it[i]) <= ITER_TOL
+        assert rel(lams[i], lam1) <= LAMBDA_RTOL
+
+
+def test_block_form_batched_matches_qp_form():
+    probs = _ragged()[:50]
+    plan = _plan(probs)
+    b = sspcg.Batch(plan, probs)
+    b.pipeline("sym")
+    lam_blk = plan.empty(sspcg.ARRAY_VEC)
+    it = torch.zeros(plan.nprob, dtype=torch.int32, device="cuda")
+    rr = torch.zeros(plan.nprob, dtype=torch.float64, device="cuda")
+    st = torch.zeros(plan.nprob, dtype=torch.int32, device="cuda")
+    sspcg.sspcg_solve_batched(plan, b.D, b.E, b.PD, b.PE, b.dev["gamma"], lam_blk, it, rr, st)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    lb = plan.unpack(sspcg.ARRAY_VEC, lam_blk, [p.gamma.shape for p in probs])
+    lq = b.lambdas()
+    assert max(rel(lb[i], lq[i]) for i in range(len(probs))) <= 1e-4
+    assert np.abs(it.cpu().numpy() - b.iters.cpu().numpy()).max() <= ITER_TOL
+
+
+def test_host_buffer_pipeline_matches_device_pipeline():
+    probs = _ragged()[:30]
+    plan = _plan(probs)
+    b = sspcg.Batch(plan, probs, pin=True)
+    b.pipeline("sym")
+    torch.cuda.synchronize()
+    h = b.host
+    lam = torch.zeros(max(int(plan.sizes[sspcg.ARRAY_VEC]), 4)).pin_memory()
+    it = torch.zeros(plan.nprob, dtype=torch.int32).pin_memory()
+    rr = torch.zeros(plan.nprob, dtype=torch.float64).pin_memory()
+    st = torch.zeros(plan.nprob, dtype=torch.int32).pin_memory()
+    sspcg.sspcg_pipeline_host(plan, "sym", h["A"], h["B"], h["qd"], h["rd"], h["gamma"], lam, it, rr, st)
+    assert torch.equal(lam, b.lam.cpu()) and torch.equal(it, b.iters.cpu())
+
+
+def test_full_size_ragged_batch_sampled_against_oracle():
+    """All 4096 problems of the ragged workload, in the benchmark's launch configuration;
+    48 sampled problems against the oracle one by one, and properties on every problem."""
+    w = P.RAGGED_BATCH_4096
+    probs = P.make_workload(w)
+    plan = _plan(probs, tol=w.tol)
+    b = sspcg.Batch(plan, probs)
+    b.pipeline("sym")
+    torch.cuda.synchronize()
+    st = b.status.cpu().numpy(); rr = b.relres.cpu().numpy(); it = b.iters.cpu().numpy()
+    assert (st == 0).all() and (rr <= w.tol).all() and (it > 0).all()
+    rt = torch.zeros(plan.nprob, dtype=torch.float64, device="cuda")
+    d = b.dev
+    sspcg.sspcg_residual_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.lam, rt)
+    torch.cuda.synchronize()
+    assert (rt.cpu().numpy() <= 1e-5).all()
+    idx = np.random.default_rng(1).choice(len(probs), 48, replace=False)
+    sample = [probs[i] for i in idx]
+    xs, it_o, _, st_o, _, _ = block.solve_batch(sample, "sym", w.tol)
+    lams = b.lambdas()
+    for j, i in enumerate(idx):
+        assert abs(it[i] - it_o[j]) <= ITER_TOL
+        assert rel(lams[i], xs[j]) <= LAMBDA_RTOL
