@@ -183,16 +183,11 @@ def main():
     b = sspcg.Batch(plan, probs, pin=True)
     d = b.dev
     stream = torch.cuda.Stream()
+    sspcg.sspcg_plan_set_timing(plan, True)
 
-    def step(ev_mid=None, ev_end=None):
-        sspcg.sspcg_build_schur_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.D, b.E, stream)
-        sspcg.sspcg_build_precond_batched(plan, PRECOND, b.D, b.E, b.PD, b.PE, b.status, stream)
-        if ev_mid is not None:
-            ev_mid.record(stream)
-        sspcg.sspcg_solve_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE, d["gamma"], b.lam,
-                                     b.iters, b.relres, b.status, stream)
-        if ev_end is not None:
-            ev_end.record(stream)
+    def step():
+        sspcg.sspcg_pipeline_batched(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD,
+                                     b.PE, b.lam, b.iters, b.relres, b.status, stream)
 
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
@@ -203,17 +198,18 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    pcg_ms, build_ms = [], []
     torch.cuda.synchronize()
     ev0.record(stream)
     for k in range(args.steps):
-        step(mids[k], ends[k])
+        step()
+        bms, pms = sspcg.sspcg_plan_timings(plan)  # CUDA events recorded on `stream` around the phases
+        build_ms.append(bms)
+        pcg_ms.append(pms)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = ev0.elapsed_time(ev1)
-    pcg_ms = [mids[k].elapsed_time(ends[k]) for k in range(args.steps)]
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -276,17 +272,20 @@ def main():
                      "frac": achieved_gbs / smem_peak_gbs, "traffic": None,
                      "kernel": "pcg_kernel (all PCG launches of a step)",
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk "
-                                    f"x {sm_max:.0f} MHz",
-                     "hbm_frac_of_measured": achieved_gbs / 6782.1},
+                                    f"x {sm_max:.0f} MHz"},
         "e2e": {"value": world * nprob * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": None,
         "clocks": clk,
     }
     # kernels of one step: Schur build, preconditioner diagonal + off-diagonal, one PCG launch per group
-    line["gpu_launches"] = args.steps * (3 + stats["qp_launches"])
-    line["schedules"] = {"resident_problems": stats["qp_resident"], "streamed_problems": stats["qp_stream"],
-                         "pcg_launches_per_step": stats["qp_launches"]}
+    fp64_builds = 3 if stats["pipeline_f64"] else 0
+    line["gpu_launches"] = args.steps * (3 + fp64_builds + stats["pipeline_launches"])
+    line["schedules"] = {"resident_fp32_problems": stats["pipeline_resident"],
+                         "streamed_fp32_problems": stats["pipeline_stream"],
+                         "fp64_problems": stats["pipeline_f64"],
+                         "pcg_launches_per_step": stats["pipeline_launches"]}
+    line["build_ms_per_step"] = statistics.mean(build_ms)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(probs, args.cpu_seconds, w.tol)
     print(json.dumps(line), flush=True)

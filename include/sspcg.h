@@ -98,6 +98,15 @@ enum {
   SSPCG_REDUCE_F64 = 2, /* FP64 products and sums (GB300 runs FP64 at ~1/64 of FP32) */
 };
 
+/* Working precision of the batched pipeline calls (sspcg_pipeline_batched,
+ * sspcg_pipeline_host, captured pipelines).  The other batched calls are FP32. */
+enum {
+  SSPCG_PRECISION_AUTO = 0, /* FP32; FP64 for problems of at most 192 unknowns ((N+1) nx), whose FP32
+                               CG loses the finite termination the clustered spectrum gives (Thm. 4.2) */
+  SSPCG_PRECISION_F32 = 1,  /* FP32 for every problem */
+  SSPCG_PRECISION_F64 = 2,  /* FP64 for every problem (blocks in plan-owned FP64 memory) */
+};
+
 /* Kernel schedule of a PCG problem. */
 enum {
   SSPCG_SCHED_AUTO = 0,     /* resident when the problem fits in one CTA's shared memory */
@@ -115,6 +124,7 @@ typedef struct {
   int32_t reduction;       /* SSPCG_REDUCE_* */
   int32_t schedule;        /* SSPCG_SCHED_*; RESIDENT is downgraded to STREAM for problems that do not fit */
   int32_t block_threads;   /* threads per CTA, multiple of 32 in [32, 512]; 0: chosen by the library */
+  int32_t precision;       /* SSPCG_PRECISION_*: working precision of the batched pipeline calls */
 } sspcg_options;
 
 /* Message of the last CUDA error seen by this thread (static storage, never NULL). */
@@ -171,6 +181,24 @@ sspcg_status sspcg_solve_qp(int32_t N, int32_t nx, int32_t nu, const float *A, c
                             sspcg_stream stream);
 
 /*
+ * FP64 path of the same three steps (the working precision of blocks,
+ * vectors and lambda is double; inputs stay FP32 and convert exactly).  For
+ * problems whose FP64 iteration count must be reproduced: FP32 rounding of
+ * Phi^-1 or of the vectors splits the doubled eigenvalue clusters of
+ * Thm. 4.2 by ~1e-7 and delays CG's finite termination (e.g. 21 -> 25..42
+ * iterations on nx = 2, N = 20).  FP64 runs at about 1/64 of the FP32 rate
+ * on GB300, so this path suits small problems.
+ */
+sspcg_status sspcg_build_schur_f64(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B,
+                                   const float *qd, const float *rd, double *D, double *E, sspcg_stream stream);
+sspcg_status sspcg_build_precond_f64(int32_t N, int32_t nx, sspcg_precond kind, const double *D, const double *E,
+                                     double *PD, double *PE, int32_t *status, sspcg_stream stream);
+sspcg_status sspcg_solve_qp_f64(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
+                                const float *rd, const double *PD, const double *PE, const float *gamma,
+                                double *lambda, const sspcg_options *opts, int32_t *iters, double *relres,
+                                int32_t *status, sspcg_stream stream);
+
+/*
  * True residual ||gamma - S lambda||_2 / ||gamma||_2 with S = C G^-1 C^T
  * applied in FP64 from the QP data (diagnostic).  relres_true: device, 1 double.
  */
@@ -215,11 +243,23 @@ sspcg_status sspcg_plan_sizes(const sspcg_plan *plan, int64_t *out);
 sspcg_status sspcg_plan_offsets(const sspcg_plan *plan, sspcg_array kind, int64_t *out);
 
 /*
- * Schedule summary (host out[6]): for the factored-S solve, the number of PCG
- * launches, of problems staged in shared memory and of problems streamed
- * from L2/HBM; then the same three for the block-S solve.
+ * Schedule summary (host out[8]): [0] PCG launches of a pipeline call, [1]
+ * FP32 problems staged in shared memory, [2] FP32 problems streamed from
+ * L2/HBM, [3] FP64 problems, [4] PCG launches of sspcg_solve_qp_batched,
+ * [5] of sspcg_solve_batched, [6]/[7] resident/streamed problems of
+ * sspcg_solve_qp_batched.
  */
 sspcg_status sspcg_plan_stats(const sspcg_plan *plan, int64_t *out);
+
+/*
+ * Phase timing.  When enabled, the plan records CUDA events on the call's
+ * stream around the preconditioner build and the PCG launches of each
+ * pipeline or solve call; sspcg_plan_timings waits for the last call and
+ * returns out_ms[0] = build time (0 for solve-only calls), out_ms[1] = PCG
+ * time.  Disabled while capturing a graph.
+ */
+sspcg_status sspcg_plan_set_timing(sspcg_plan *plan, int32_t enable);
+sspcg_status sspcg_plan_timings(sspcg_plan *plan, float *out_ms);
 
 /* Batched sspcg_build_schur over packed arrays. */
 sspcg_status sspcg_build_schur_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
@@ -255,6 +295,18 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
                                     const float *qd, const float *rd, const float *gamma, float *D, float *E,
                                     float *PD, float *PE, float *lambda, int32_t *iters, double *relres,
                                     int32_t *status, sspcg_stream stream);
+
+/*
+ * Capture sspcg_pipeline_batched with these pointers into a CUDA graph owned
+ * by the plan (the call first runs the pipeline once uncaptured); then
+ * sspcg_plan_launch replays it.  ``stream`` must not be the legacy default
+ * stream.  A later capture replaces the graph.
+ */
+sspcg_status sspcg_plan_capture_pipeline(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
+                                         const float *qd, const float *rd, const float *gamma, float *D, float *E,
+                                         float *PD, float *PE, float *lambda, int32_t *iters, double *relres,
+                                         int32_t *status, sspcg_stream stream);
+sspcg_status sspcg_plan_launch(sspcg_plan *plan, sspcg_stream stream);
 
 /*
  * sspcg_pipeline_batched from HOST buffers (packed like the device arrays):

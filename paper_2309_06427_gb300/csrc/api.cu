@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <numeric>
 #include <vector>
 
@@ -69,8 +70,8 @@ int red_mode(int32_t r) {
   return kRedDf;
 }
 
-int64_t pcg_smem_bytes(int op, bool res, int N, int nx, int nu) {
-  return pcg_layout(op, res, N, nx, nu).total * (int64_t)sizeof(float);
+int64_t pcg_smem_bytes(int op, bool res, int N, int nx, int nu, bool f64 = false) {
+  return pcg_layout(op, res, N, nx, nu).total * (int64_t)(f64 ? sizeof(double) : sizeof(float));
 }
 
 int64_t smem_budget() { return (int64_t)max_smem_optin() - kPcgStaticSmem; }  // bytes of dynamic smem
@@ -83,10 +84,10 @@ int auto_block(int64_t rows) {
 
 // Choose residency for a problem; returns false when even the streaming
 // layout does not fit.
-bool choose_resident(int op, int sched, int N, int nx, int nu, bool *resident) {
+bool choose_resident(int op, int sched, int N, int nx, int nu, bool *resident, bool f64 = false) {
   const int64_t budget = smem_budget();
-  const bool fits_res = pcg_smem_bytes(op, true, N, nx, nu) <= budget;
-  const bool fits_str = pcg_smem_bytes(op, false, N, nx, nu) <= budget;
+  const bool fits_res = pcg_smem_bytes(op, true, N, nx, nu, f64) <= budget;
+  const bool fits_str = pcg_smem_bytes(op, false, N, nx, nu, f64) <= budget;
   if (!fits_str) return false;
   *resident = (sched != SSPCG_SCHED_STREAM) && fits_res;
   return true;
@@ -100,6 +101,7 @@ sspcg_status validate_opts(const sspcg_options *o) {
   if (o->schedule < 0 || o->schedule > 2) return SSPCG_ERR_INVALID_ARG;
   if (o->block_threads != 0 && (o->block_threads < 32 || o->block_threads > 512 || o->block_threads % 32))
     return SSPCG_ERR_INVALID_ARG;
+  if (o->precision < 0 || o->precision > 2) return SSPCG_ERR_INVALID_ARG;
   return SSPCG_OK;
 }
 
@@ -113,9 +115,16 @@ int pcg_max_smem_bytes() { return max_smem_optin() - kPcgStaticSmem; }
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
+// Problems with at most this many unknowns ((N+1)*nx) take the FP64 path in
+// the pipeline calls under SSPCG_PRECISION_AUTO: in FP32 their CG loses the
+// finite termination that the clustered spectrum of Thm. 4.2 gives in exact
+// arithmetic (a few extra iterations), and at this size FP64 costs little.
+constexpr int64_t kTinyUnknowns = 192;
+
 struct PcgGroup {
   int nx = 0;
   bool resident = false;
+  bool f64 = false;
   int block = 0;
   int grid = 0;
   size_t smem = 0;
@@ -123,6 +132,16 @@ struct PcgGroup {
   int32_t nwork = 0;
   int counter_index = 0;
 };
+
+// A set of problems solved by one group of PCG launches (one per nx and schedule).
+struct GroupSet {
+  int op = kOpQp;
+  bool f64 = false;
+  std::vector<PcgGroup> groups;
+  int64_t n_resident = 0, n_stream = 0;
+};
+
+enum { kSetQpAll = 0, kSetBlockAll = 1, kSetQpMain = 2, kSetTiny = 3, kNumSets = 4 };
 
 struct sspcg_plan {
   int32_t nprob = 0;
@@ -133,13 +152,26 @@ struct sspcg_plan {
   ProbDesc *d_desc = nullptr;
   int64_t *d_knot_start = nullptr, *d_off_start = nullptr;
   int64_t total_knots = 0, total_off = 0;
-  int32_t *d_work = nullptr;      // 2 * nprob: QP-form groups then block-form groups
-  int32_t *d_counters = nullptr;  // one per group
-  std::vector<PcgGroup> groups[2];  // [op]
+  // FP64 subset: descriptors whose odiag/ooff point into plan-owned FP64 blocks
+  int32_t ntiny = 0;
+  std::vector<ProbDesc> tdesc;
+  ProbDesc *d_tdesc = nullptr;
+  int64_t *d_tknot_start = nullptr, *d_toff_start = nullptr;
+  int64_t tknots = 0, toff = 0, t_diag = 0, t_offe = 0;
+  double *D64 = nullptr, *E64 = nullptr, *PD64 = nullptr, *PE64 = nullptr;
+  // PCG launch groups
+  int32_t *d_work = nullptr;
+  int32_t *d_counters = nullptr;
   int ngroups_total = 0;
-  // side streams for concurrent group launches
+  GroupSet sets[kNumSets];
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;
+  // phase timing (opt-in)
+  bool timing = false;
+  cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
+  bool build_timed = false;
+  // captured pipeline
+  cudaGraphExec_t graph = nullptr;
   // plan-owned device buffers of the host pipeline
   float *hbuf = nullptr;
   int64_t hbuf_floats = 0;
@@ -151,86 +183,58 @@ namespace {
 
 void plan_free(sspcg_plan *p) {
   if (!p) return;
-  cudaFree(p->d_desc);
-  cudaFree(p->d_knot_start);
-  cudaFree(p->d_off_start);
-  cudaFree(p->d_work);
-  cudaFree(p->d_counters);
-  cudaFree(p->hbuf);
-  cudaFree(p->hint);
-  cudaFree(p->hdbl);
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  for (void *ptr : {(void *)p->d_desc, (void *)p->d_knot_start, (void *)p->d_off_start, (void *)p->d_tdesc,
+                    (void *)p->d_tknot_start, (void *)p->d_toff_start, (void *)p->D64, (void *)p->E64,
+                    (void *)p->PD64, (void *)p->PE64, (void *)p->d_work, (void *)p->d_counters, (void *)p->hbuf,
+                    (void *)p->hint, (void *)p->hdbl})
+    cudaFree(ptr);
   for (auto s : p->side) cudaStreamDestroy(s);
   for (auto e : p->ev) cudaEventDestroy(e);
+  for (auto e : p->tev)
+    if (e) cudaEventDestroy(e);
   delete p;
 }
 
-// Build the PCG launch groups of one operator form: problems grouped by
-// (nx, residency), each group's work list ordered largest first.
-sspcg_status plan_groups(sspcg_plan *p, int op, std::vector<int32_t> &work_host, int32_t base) {
+// PCG launch groups of one set: its members grouped by (nx, residency), each
+// group's work list ordered largest first.  ``members`` index ``descs``.
+sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDesc> &descs,
+                         const std::vector<int32_t> &members, std::vector<int32_t> &work_host, int32_t &pos) {
   std::vector<std::vector<int32_t>> buckets(2 * (kMaxNx + 1));
-  for (int32_t i = 0; i < p->nprob; ++i) {
-    const ProbDesc &d = p->hdesc[i];
+  for (int32_t i : members) {
+    const ProbDesc &d = descs[i];
     bool res = false;
-    if (!choose_resident(op, p->opts.schedule, d.N, d.nx, d.nu, &res)) return SSPCG_ERR_UNSUPPORTED;
+    if (!choose_resident(set.op, p->opts.schedule, d.N, d.nx, d.nu, &res, set.f64)) return SSPCG_ERR_UNSUPPORTED;
     buckets[2 * d.nx + (res ? 1 : 0)].push_back(i);
   }
-  int32_t pos = base;
   for (int nx = 1; nx <= kMaxNx; ++nx) {
     for (int r = 0; r < 2; ++r) {
       auto &b = buckets[2 * nx + r];
       if (b.empty()) continue;
-      std::stable_sort(b.begin(), b.end(), [&](int32_t x, int32_t y) {
-        return p->hdesc[x].N > p->hdesc[y].N;  // same nx: cost grows with N
-      });
+      std::stable_sort(b.begin(), b.end(), [&](int32_t x, int32_t y) { return descs[x].N > descs[y].N; });
       PcgGroup g;
       g.nx = nx;
       g.resident = r == 1;
+      g.f64 = set.f64;
       int64_t maxrows = 0, maxsmem = 0;
       for (int32_t i : b) {
-        const ProbDesc &d = p->hdesc[i];
+        const ProbDesc &d = descs[i];
         maxrows = std::max<int64_t>(maxrows, (int64_t)(d.N + 1) * d.nx);
-        maxsmem = std::max<int64_t>(maxsmem, pcg_smem_bytes(op, g.resident, d.N, d.nx, d.nu));
+        maxsmem = std::max<int64_t>(maxsmem, pcg_smem_bytes(set.op, g.resident, d.N, d.nx, d.nu, set.f64));
       }
       g.block = p->opts.block_threads > 0 ? p->opts.block_threads : auto_block(maxrows);
       g.smem = (size_t)maxsmem;
       const int64_t per_sm_smem = 228 * 1024;
-      int by_smem = (int)std::max<int64_t>(1, per_sm_smem / (maxsmem + kPcgStaticSmem + 1024));
-      int by_thr = std::max(1, 2048 / g.block);
-      int per_sm = std::min(by_smem, by_thr);
-      g.grid = (int)std::min<int64_t>((int64_t)b.size(), (int64_t)per_sm * device_sms());
+      const int by_smem = (int)std::max<int64_t>(1, per_sm_smem / (maxsmem + kPcgStaticSmem + 1024));
+      const int by_thr = std::max(1, 2048 / g.block);
+      g.grid = (int)std::min<int64_t>((int64_t)b.size(), (int64_t)std::min(by_smem, by_thr) * device_sms());
       g.nwork = (int32_t)b.size();
       g.d_work = p->d_work + pos;
       g.counter_index = p->ngroups_total++;
       for (int32_t i : b) work_host[pos++] = i;
-      p->groups[op].push_back(g);
+      (g.resident ? set.n_resident : set.n_stream) += g.nwork;
+      set.groups.push_back(g);
     }
-  }
-  return SSPCG_OK;
-}
-
-sspcg_status launch_groups(sspcg_plan *p, int op, const PcgArgs &base, cudaStream_t st) {
-  auto &groups = p->groups[op];
-  if (groups.empty()) return SSPCG_OK;
-  SSPCG_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int32_t) * p->ngroups_total, st));
-  const size_t ng = groups.size();
-  // fork: side streams wait for the main stream
-  if (ng > 1) {
-    SSPCG_CUDA(cudaEventRecord(p->ev[0], st));
-    for (size_t i = 1; i < ng; ++i) SSPCG_CUDA(cudaStreamWaitEvent(p->side[i - 1], p->ev[0], 0));
-  }
-  for (size_t i = 0; i < ng; ++i) {
-    const PcgGroup &g = groups[i];
-    PcgArgs a = base;
-    a.work = g.d_work;
-    a.nwork = g.nwork;
-    a.counter = p->d_counters + g.counter_index;
-    cudaStream_t s = i == 0 ? st : p->side[i - 1];
-    SSPCG_CUDA(launch_pcg(g.nx, op, red_mode(p->opts.reduction), g.resident, a, g.grid, g.block, g.smem, s));
-  }
-  // join
-  for (size_t i = 1; i < ng; ++i) {
-    SSPCG_CUDA(cudaEventRecord(p->ev[i], p->side[i - 1]));
-    SSPCG_CUDA(cudaStreamWaitEvent(st, p->ev[i], 0));
   }
   return SSPCG_OK;
 }
@@ -240,11 +244,63 @@ PcgArgs make_args(const sspcg_options *o) {
   a.tol2 = (float)(o->tol * o->tol);
   a.max_iter = o->max_iter;
   a.warm = o->warm_start;
+  a.lambda_f32 = 1;
   return a;
 }
 
-}  // namespace
+struct SetLaunch {
+  const GroupSet *set;
+  PcgArgs args;
+};
 
+// Launch the groups of several sets concurrently: fork side streams off
+// ``st``, one group per stream, join back.
+sspcg_status launch_sets(sspcg_plan *p, std::initializer_list<SetLaunch> list, cudaStream_t st) {
+  struct Item {
+    const PcgGroup *g;
+    const PcgArgs *a;
+    int op;
+  };
+  std::vector<Item> all;
+  for (const SetLaunch &sl : list)
+    for (const PcgGroup &g : sl.set->groups) all.push_back({&g, &sl.args, sl.set->op});
+  if (all.empty()) return SSPCG_OK;
+  SSPCG_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int32_t) * p->ngroups_total, st));
+  const size_t ng = all.size();
+  if (ng > 1) {
+    SSPCG_CUDA(cudaEventRecord(p->ev[0], st));
+    for (size_t i = 1; i < ng; ++i) SSPCG_CUDA(cudaStreamWaitEvent(p->side[i - 1], p->ev[0], 0));
+  }
+  for (size_t i = 0; i < ng; ++i) {
+    const PcgGroup &g = *all[i].g;
+    PcgArgs a = *all[i].a;
+    a.work = g.d_work;
+    a.nwork = g.nwork;
+    a.counter = p->d_counters + g.counter_index;
+    cudaStream_t s = i == 0 ? st : p->side[i - 1];
+    const int red = g.f64 ? kRedF64 : red_mode(p->opts.reduction);
+    SSPCG_CUDA(launch_pcg(g.nx, all[i].op, red, g.resident, g.f64, a, g.grid, g.block, g.smem, s));
+  }
+  for (size_t i = 1; i < ng; ++i) {
+    SSPCG_CUDA(cudaEventRecord(p->ev[i], p->side[i - 1]));
+    SSPCG_CUDA(cudaStreamWaitEvent(st, p->ev[i], 0));
+  }
+  return SSPCG_OK;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &src) {
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(dst, sizeof(T) * src.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+void time_mark(sspcg_plan *p, int i, cudaStream_t st) {
+  if (p->timing) cudaEventRecord(p->tev[i], st);
+}
+
+}  // namespace
 extern "C" {
 
 const char *sspcg_last_cuda_error(void) { return g_cuda_err; }
@@ -255,7 +311,28 @@ sspcg_status sspcg_build_schur(int32_t N, int32_t nx, int32_t nu, const float *A
   if (!shape_ok(N, nx, nu)) return SSPCG_ERR_INVALID_ARG;
   if (!qd || !D || (N > 0 && (!A || !rd || !E || (nu > 0 && !B)))) return SSPCG_ERR_INVALID_ARG;
   ProbSet ps{nullptr, single_desc(N, nx, nu), 1};
-  SSPCG_CUDA(launch_schur_build(ps, nullptr, N + 1, A, B, qd, rd, D, E, (cudaStream_t)stream, device_sms()));
+  SSPCG_CUDA(launch_schur_build<float>(ps, nullptr, N + 1, A, B, qd, rd, D, E, (cudaStream_t)stream, device_sms()));
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_build_schur_f64(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
+                                   const float *rd, double *D, double *E, sspcg_stream stream) {
+  if (!shape_ok(N, nx, nu)) return SSPCG_ERR_INVALID_ARG;
+  if (!qd || !D || (N > 0 && (!A || !rd || !E || (nu > 0 && !B)))) return SSPCG_ERR_INVALID_ARG;
+  ProbSet ps{nullptr, single_desc(N, nx, nu), 1};
+  SSPCG_CUDA(launch_schur_build<double>(ps, nullptr, N + 1, A, B, qd, rd, D, E, (cudaStream_t)stream, device_sms()));
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_build_precond_f64(int32_t N, int32_t nx, sspcg_precond kind, const double *D, const double *E,
+                                     double *PD, double *PE, int32_t *status, sspcg_stream stream) {
+  if (!shape_ok(N, nx, 0) || kind < 0 || kind > 3) return SSPCG_ERR_INVALID_ARG;
+  if (!D || !PD || !status || (N > 0 && (!E || !PE))) return SSPCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ProbSet ps{nullptr, single_desc(N, nx, 0), 1};
+  SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+  SSPCG_CUDA(launch_precond_build<double>(ps, nullptr, N + 1, nullptr, N, (int)kind, D, E, PD, PE, status, st,
+                                          device_sms(), (int64_t)N * nx * nx));
   return SSPCG_OK;
 }
 
@@ -266,48 +343,58 @@ sspcg_status sspcg_build_precond(int32_t N, int32_t nx, sspcg_precond kind, cons
   cudaStream_t st = (cudaStream_t)stream;
   ProbSet ps{nullptr, single_desc(N, nx, 0), 1};
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-  SSPCG_CUDA(launch_precond_build(ps, nullptr, N + 1, nullptr, N, (int)kind, D, E, PD, PE, status, st, device_sms(),
-                                  (int64_t)N * nx * nx));
+  SSPCG_CUDA(launch_precond_build<float>(ps, nullptr, N + 1, nullptr, N, (int)kind, D, E, PD, PE, status, st,
+                                         device_sms(), (int64_t)N * nx * nx));
   return SSPCG_OK;
 }
 
-static sspcg_status solve_single(int op, int32_t N, int32_t nx, int32_t nu, const float *A, const float *B,
-                                 const float *qd, const float *rd, const float *D, const float *E, const float *PD,
-                                 const float *PE, const float *gamma, float *lambda, const sspcg_options *opts,
-                                 int32_t *iters, double *relres, int32_t *status, sspcg_stream stream) {
+static sspcg_status solve_single(int op, bool f64, int32_t N, int32_t nx, int32_t nu, const float *A,
+                                 const float *B, const float *qd, const float *rd, const float *D, const float *E,
+                                 const void *PD, const void *PE, const float *gamma, void *lambda,
+                                 const sspcg_options *opts, int32_t *iters, double *relres, int32_t *status,
+                                 sspcg_stream stream) {
   if (validate_opts(opts) != SSPCG_OK) return SSPCG_ERR_INVALID_ARG;
   if (!shape_ok(N, nx, nu)) return SSPCG_ERR_INVALID_ARG;
   if (!PD || !gamma || !lambda || !iters || !relres || !status || (N > 0 && !PE)) return SSPCG_ERR_INVALID_ARG;
   if (op == kOpQp && (!qd || (N > 0 && (!A || !rd || (nu > 0 && !B))))) return SSPCG_ERR_INVALID_ARG;
   if (op == kOpBlock && (!D || (N > 0 && !E))) return SSPCG_ERR_INVALID_ARG;
   bool res = false;
-  if (!choose_resident(op, opts->schedule, N, nx, nu, &res)) return SSPCG_ERR_UNSUPPORTED;
+  if (!choose_resident(op, opts->schedule, N, nx, nu, &res, f64)) return SSPCG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   PcgArgs a = make_args(opts);
   a.ps = ProbSet{nullptr, single_desc(N, nx, nu), 1};
   a.work = nullptr; a.nwork = 1; a.counter = nullptr;
   a.A = A; a.B = B; a.qd = qd; a.rd = rd; a.D = D; a.E = E; a.PD = PD; a.PE = PE;
   a.gamma = gamma; a.lambda = lambda; a.iters = iters; a.relres = relres; a.status = status;
+  a.lambda_f32 = f64 ? 0 : 1;
   const int block = opts->block_threads > 0 ? opts->block_threads : auto_block((int64_t)(N + 1) * nx);
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-  SSPCG_CUDA(launch_pcg(nx, op, red_mode(opts->reduction), res, a, 1, block,
-                        (size_t)pcg_smem_bytes(op, res, N, nx, nu), st));
+  SSPCG_CUDA(launch_pcg(nx, op, f64 ? kRedF64 : red_mode(opts->reduction), res, f64, a, 1, block,
+                        (size_t)pcg_smem_bytes(op, res, N, nx, nu, f64), st));
   return SSPCG_OK;
 }
 
 sspcg_status sspcg_solve(int32_t N, int32_t nx, const float *D, const float *E, const float *PD, const float *PE,
                          const float *gamma, float *lambda, const sspcg_options *opts, int32_t *iters,
                          double *relres, int32_t *status, sspcg_stream stream) {
-  return solve_single(kOpBlock, N, nx, 0, nullptr, nullptr, nullptr, nullptr, D, E, PD, PE, gamma, lambda, opts,
-                      iters, relres, status, stream);
+  return solve_single(kOpBlock, false, N, nx, 0, nullptr, nullptr, nullptr, nullptr, D, E, PD, PE, gamma, lambda,
+                      opts, iters, relres, status, stream);
 }
 
 sspcg_status sspcg_solve_qp(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
                             const float *rd, const float *PD, const float *PE, const float *gamma, float *lambda,
                             const sspcg_options *opts, int32_t *iters, double *relres, int32_t *status,
                             sspcg_stream stream) {
-  return solve_single(kOpQp, N, nx, nu, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, opts, iters, relres,
-                      status, stream);
+  return solve_single(kOpQp, false, N, nx, nu, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, opts, iters,
+                      relres, status, stream);
+}
+
+sspcg_status sspcg_solve_qp_f64(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
+                                const float *rd, const double *PD, const double *PE, const float *gamma,
+                                double *lambda, const sspcg_options *opts, int32_t *iters, double *relres,
+                                int32_t *status, sspcg_stream stream) {
+  return solve_single(kOpQp, true, N, nx, nu, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, opts, iters,
+                      relres, status, stream);
 }
 
 sspcg_status sspcg_residual_qp(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
@@ -337,6 +424,7 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
   for (int k = 0; k < SSPCG_NUM_ARRAYS; ++k) p->offsets[k].resize(nprob);
   std::vector<int64_t> knot_start(nprob + 1, 0), off_start(nprob + 1, 0);
   int64_t cur[SSPCG_NUM_ARRAYS] = {};
+  std::vector<int32_t> all, main_set, tiny;
   for (int32_t i = 0; i < nprob; ++i) {
     const int64_t n = N[i] + 1, m = nx[i], u = nu[i], Ni = N[i];
     const int64_t sz[SSPCG_NUM_ARRAYS] = {Ni * m * m, Ni * m * u, n * m, Ni * u, n * m * m, Ni * m * m, n * m};
@@ -345,7 +433,7 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
       cur[k] += round_up(sz[k], 4);  // 16-byte aligned problem starts
     }
     ProbDesc &d = p->hdesc[i];
-    d.N = N[i]; d.nx = nx[i]; d.nu = nu[i];
+    d.N = N[i]; d.nx = nx[i]; d.nu = nu[i]; d.id = i;
     d.oA = p->offsets[SSPCG_ARRAY_A][i];
     d.oB = p->offsets[SSPCG_ARRAY_B][i];
     d.oq = p->offsets[SSPCG_ARRAY_QD][i];
@@ -355,35 +443,69 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     d.ovec = p->offsets[SSPCG_ARRAY_VEC][i];
     knot_start[i + 1] = knot_start[i] + n;
     off_start[i + 1] = off_start[i] + Ni;
+    all.push_back(i);
+    const bool f64 = opts->precision == SSPCG_PRECISION_F64 ||
+                     (opts->precision == SSPCG_PRECISION_AUTO && n * m <= kTinyUnknowns);
+    (f64 ? tiny : main_set).push_back(i);
   }
   for (int k = 0; k < SSPCG_NUM_ARRAYS; ++k) p->sizes[k] = cur[k];
   p->total_knots = knot_start[nprob];
   p->total_off = off_start[nprob];
+  // FP64 subset: same inputs, FP64 blocks in plan memory
+  p->ntiny = (int32_t)tiny.size();
+  std::vector<int64_t> tknot(p->ntiny + 1, 0), toff(p->ntiny + 1, 0);
+  for (int32_t t = 0; t < p->ntiny; ++t) {
+    ProbDesc d = p->hdesc[tiny[t]];
+    const int64_t n = d.N + 1, m = d.nx;
+    d.odiag = p->t_diag;
+    d.ooff = p->t_offe;
+    p->t_diag += round_up(n * m * m, 2);
+    p->t_offe += round_up((int64_t)d.N * m * m, 2);
+    p->tdesc.push_back(d);
+    tknot[t + 1] = tknot[t] + n;
+    toff[t + 1] = toff[t] + d.N;
+  }
+  p->tknots = tknot[p->ntiny];
+  p->toff = toff[p->ntiny];
   auto fail = [&](sspcg_status s) { plan_free(p); return s; };
   if (nprob > 0) {
     cudaError_t e;
-    if ((e = cudaMalloc(&p->d_desc, sizeof(ProbDesc) * nprob)) != cudaSuccess) return fail(cuda_fail(e));
-    if ((e = cudaMalloc(&p->d_knot_start, sizeof(int64_t) * (nprob + 1))) != cudaSuccess) return fail(cuda_fail(e));
-    if ((e = cudaMalloc(&p->d_off_start, sizeof(int64_t) * (nprob + 1))) != cudaSuccess) return fail(cuda_fail(e));
-    if ((e = cudaMalloc(&p->d_work, sizeof(int32_t) * 2 * nprob)) != cudaSuccess) return fail(cuda_fail(e));
-    if ((e = cudaMemcpy(p->d_desc, p->hdesc.data(), sizeof(ProbDesc) * nprob, cudaMemcpyHostToDevice)) != cudaSuccess)
-      return fail(cuda_fail(e));
-    if ((e = cudaMemcpy(p->d_knot_start, knot_start.data(), sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice)) !=
-        cudaSuccess)
-      return fail(cuda_fail(e));
-    if ((e = cudaMemcpy(p->d_off_start, off_start.data(), sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice)) !=
-        cudaSuccess)
-      return fail(cuda_fail(e));
-    std::vector<int32_t> work(2 * nprob);
-    sspcg_status s = plan_groups(p, kOpQp, work, 0);
-    if (s != SSPCG_OK) return fail(s);
-    s = plan_groups(p, kOpBlock, work, nprob);
-    if (s != SSPCG_OK) return fail(s);
-    if ((e = cudaMemcpy(p->d_work, work.data(), sizeof(int32_t) * 2 * nprob, cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = upload(&p->d_desc, p->hdesc)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = upload(&p->d_knot_start, knot_start)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = upload(&p->d_off_start, off_start)) != cudaSuccess) return fail(cuda_fail(e));
+    if (p->ntiny > 0) {
+      if ((e = upload(&p->d_tdesc, p->tdesc)) != cudaSuccess) return fail(cuda_fail(e));
+      if ((e = upload(&p->d_tknot_start, tknot)) != cudaSuccess) return fail(cuda_fail(e));
+      if ((e = upload(&p->d_toff_start, toff)) != cudaSuccess) return fail(cuda_fail(e));
+      const int64_t td = std::max<int64_t>(p->t_diag, 2), to = std::max<int64_t>(p->t_offe, 2);
+      if ((e = cudaMalloc(&p->D64, sizeof(double) * td)) != cudaSuccess) return fail(cuda_fail(e));
+      if ((e = cudaMalloc(&p->PD64, sizeof(double) * td)) != cudaSuccess) return fail(cuda_fail(e));
+      if ((e = cudaMalloc(&p->E64, sizeof(double) * to)) != cudaSuccess) return fail(cuda_fail(e));
+      if ((e = cudaMalloc(&p->PE64, sizeof(double) * to)) != cudaSuccess) return fail(cuda_fail(e));
+    }
+    const size_t nwork = 2 * (size_t)nprob + main_set.size() + tiny.size();
+    if ((e = cudaMalloc(&p->d_work, sizeof(int32_t) * nwork)) != cudaSuccess) return fail(cuda_fail(e));
+    std::vector<int32_t> work(nwork);
+    std::vector<int32_t> tiny_local(p->ntiny);
+    std::iota(tiny_local.begin(), tiny_local.end(), 0);
+    int32_t pos = 0;
+    p->sets[kSetQpAll].op = kOpQp;
+    p->sets[kSetBlockAll].op = kOpBlock;
+    p->sets[kSetQpMain].op = kOpQp;
+    p->sets[kSetTiny].op = kOpQp;
+    p->sets[kSetTiny].f64 = true;
+    sspcg_status s;
+    if ((s = plan_groups(p, p->sets[kSetQpAll], p->hdesc, all, work, pos)) != SSPCG_OK) return fail(s);
+    if ((s = plan_groups(p, p->sets[kSetBlockAll], p->hdesc, all, work, pos)) != SSPCG_OK) return fail(s);
+    if ((s = plan_groups(p, p->sets[kSetQpMain], p->hdesc, main_set, work, pos)) != SSPCG_OK) return fail(s);
+    if ((s = plan_groups(p, p->sets[kSetTiny], p->tdesc, tiny_local, work, pos)) != SSPCG_OK) return fail(s);
+    if ((e = cudaMemcpy(p->d_work, work.data(), sizeof(int32_t) * nwork, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e));
     if ((e = cudaMalloc(&p->d_counters, sizeof(int32_t) * std::max(1, p->ngroups_total))) != cudaSuccess)
       return fail(cuda_fail(e));
-    const size_t nside = std::max(p->groups[0].size(), p->groups[1].size());
+    size_t nside = 0;
+    for (int k = 0; k < kNumSets; ++k) nside = std::max(nside, p->sets[k].groups.size());
+    nside = std::max(nside, p->sets[kSetQpMain].groups.size() + p->sets[kSetTiny].groups.size());
     p->ev.resize(nside + 1);
     for (auto &ev : p->ev)
       if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(cuda_fail(e));
@@ -415,18 +537,37 @@ sspcg_status sspcg_plan_offsets(const sspcg_plan *plan, sspcg_array kind, int64_
 
 sspcg_status sspcg_plan_stats(const sspcg_plan *plan, int64_t *out) {
   if (!plan || !out) return SSPCG_ERR_INVALID_ARG;
-  for (int op = 0; op < 2; ++op) {
-    int64_t res = 0, str = 0;
-    for (const PcgGroup &g : plan->groups[op]) (g.resident ? res : str) += g.nwork;
-    const int slot = op == kOpQp ? 0 : 3;
-    out[slot] = (int64_t)plan->groups[op].size();
-    out[slot + 1] = res;
-    out[slot + 2] = str;
-  }
+  const GroupSet &m = plan->sets[kSetQpMain], &t = plan->sets[kSetTiny];
+  out[0] = (int64_t)(m.groups.size() + t.groups.size());
+  out[1] = m.n_resident;
+  out[2] = m.n_stream;
+  out[3] = plan->ntiny;
+  out[4] = (int64_t)plan->sets[kSetQpAll].groups.size();
+  out[5] = (int64_t)plan->sets[kSetBlockAll].groups.size();
+  out[6] = plan->sets[kSetQpAll].n_resident;
+  out[7] = plan->sets[kSetQpAll].n_stream;
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_plan_set_timing(sspcg_plan *plan, int32_t enable) {
+  if (!plan) return SSPCG_ERR_INVALID_ARG;
+  if (enable && !plan->tev[0])
+    for (auto &e : plan->tev) SSPCG_CUDA(cudaEventCreate(&e));
+  plan->timing = enable != 0;
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_plan_timings(sspcg_plan *plan, float *out_ms) {
+  if (!plan || !out_ms || !plan->tev[0]) return SSPCG_ERR_INVALID_ARG;
+  SSPCG_CUDA(cudaEventSynchronize(plan->tev[2]));
+  out_ms[0] = 0.0f;
+  if (plan->build_timed) SSPCG_CUDA(cudaEventElapsedTime(&out_ms[0], plan->tev[0], plan->tev[1]));
+  SSPCG_CUDA(cudaEventElapsedTime(&out_ms[1], plan->tev[1], plan->tev[2]));
   return SSPCG_OK;
 }
 
 static ProbSet plan_set(const sspcg_plan *p) { return ProbSet{p->d_desc, ProbDesc{}, p->nprob}; }
+static ProbSet tiny_set(const sspcg_plan *p) { return ProbSet{p->d_tdesc, ProbDesc{}, p->ntiny}; }
 
 sspcg_status sspcg_build_schur_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
                                        const float *rd, float *D, float *E, sspcg_stream stream) {
@@ -434,8 +575,8 @@ sspcg_status sspcg_build_schur_batched(sspcg_plan *plan, const float *A, const f
   if (plan->nprob == 0) return SSPCG_OK;
   if (!qd || !D || !aligned16(qd) || !aligned16(D)) return SSPCG_ERR_INVALID_ARG;
   if (plan->total_off > 0 && (!A || !rd || !E || !B)) return SSPCG_ERR_INVALID_ARG;
-  SSPCG_CUDA(launch_schur_build(plan_set(plan), plan->d_knot_start, plan->total_knots, A, B, qd, rd, D, E,
-                                (cudaStream_t)stream, device_sms()));
+  SSPCG_CUDA(launch_schur_build<float>(plan_set(plan), plan->d_knot_start, plan->total_knots, A, B, qd, rd, D, E,
+                                       (cudaStream_t)stream, device_sms()));
   return SSPCG_OK;
 }
 
@@ -446,44 +587,70 @@ sspcg_status sspcg_build_precond_batched(sspcg_plan *plan, sspcg_precond kind, c
   if (!D || !PD || !status || (plan->total_off > 0 && (!E || !PE))) return SSPCG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
-  SSPCG_CUDA(launch_precond_build(plan_set(plan), plan->d_knot_start, plan->total_knots, plan->d_off_start,
-                                  plan->total_off, (int)kind, D, E, PD, PE, status, st, device_sms(),
-                                  plan->sizes[SSPCG_ARRAY_OFF]));
+  SSPCG_CUDA(launch_precond_build<float>(plan_set(plan), plan->d_knot_start, plan->total_knots, plan->d_off_start,
+                                         plan->total_off, (int)kind, D, E, PD, PE, status, st, device_sms(),
+                                         plan->sizes[SSPCG_ARRAY_OFF]));
   return SSPCG_OK;
 }
 
-static sspcg_status solve_batched(sspcg_plan *plan, int op, const float *A, const float *B, const float *qd,
-                                  const float *rd, const float *D, const float *E, const float *PD, const float *PE,
-                                  const float *gamma, float *lambda, int32_t *iters, double *relres,
-                                  int32_t *status, sspcg_stream stream, bool status_in) {
-  if (!plan) return SSPCG_ERR_INVALID_ARG;
-  if (plan->nprob == 0) return SSPCG_OK;
-  if (!PD || !gamma || !lambda || !iters || !relres || !status) return SSPCG_ERR_INVALID_ARG;
-  if (plan->total_off > 0 && !PE) return SSPCG_ERR_INVALID_ARG;
-  if (op == kOpQp && (!qd || (plan->total_off > 0 && (!A || !rd || !B)))) return SSPCG_ERR_INVALID_ARG;
-  if (op == kOpBlock && (!D || (plan->total_off > 0 && !E))) return SSPCG_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (!status_in) SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
+static PcgArgs batched_args(sspcg_plan *plan, const float *A, const float *B, const float *qd, const float *rd,
+                            const float *D, const float *E, const void *PD, const void *PE, const float *gamma,
+                            float *lambda, int32_t *iters, double *relres, int32_t *status) {
   PcgArgs a = make_args(&plan->opts);
   a.ps = plan_set(plan);
   a.A = A; a.B = B; a.qd = qd; a.rd = rd; a.D = D; a.E = E; a.PD = PD; a.PE = PE;
   a.gamma = gamma; a.lambda = lambda; a.iters = iters; a.relres = relres; a.status = status;
-  return launch_groups(plan, op, a, st);
+  return a;
+}
+
+static sspcg_status check_solve_args(sspcg_plan *plan, int op, const float *A, const float *B, const float *qd,
+                                     const float *rd, const float *D, const float *E, const float *PD,
+                                     const float *PE, const float *gamma, float *lambda, int32_t *iters,
+                                     double *relres, int32_t *status) {
+  if (!PD || !gamma || !lambda || !iters || !relres || !status) return SSPCG_ERR_INVALID_ARG;
+  if (plan->total_off > 0 && !PE) return SSPCG_ERR_INVALID_ARG;
+  if (op == kOpQp && (!qd || (plan->total_off > 0 && (!A || !rd || !B)))) return SSPCG_ERR_INVALID_ARG;
+  if (op == kOpBlock && (!D || (plan->total_off > 0 && !E))) return SSPCG_ERR_INVALID_ARG;
+  return SSPCG_OK;
 }
 
 sspcg_status sspcg_solve_batched(sspcg_plan *plan, const float *D, const float *E, const float *PD,
                                  const float *PE, const float *gamma, float *lambda, int32_t *iters,
                                  double *relres, int32_t *status, sspcg_stream stream) {
-  return solve_batched(plan, kOpBlock, nullptr, nullptr, nullptr, nullptr, D, E, PD, PE, gamma, lambda, iters,
-                       relres, status, stream, false);
+  if (!plan) return SSPCG_ERR_INVALID_ARG;
+  if (plan->nprob == 0) return SSPCG_OK;
+  sspcg_status s = check_solve_args(plan, kOpBlock, nullptr, nullptr, nullptr, nullptr, D, E, PD, PE, gamma, lambda,
+                                    iters, relres, status);
+  if (s != SSPCG_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
+  plan->build_timed = false;
+  time_mark(plan, 1, st);
+  s = launch_sets(plan, {{&plan->sets[kSetBlockAll], batched_args(plan, nullptr, nullptr, nullptr, nullptr, D, E, PD,
+                                                                   PE, gamma, lambda, iters, relres, status)}},
+                  st);
+  time_mark(plan, 2, st);
+  return s;
 }
 
 sspcg_status sspcg_solve_qp_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
                                     const float *rd, const float *PD, const float *PE, const float *gamma,
                                     float *lambda, int32_t *iters, double *relres, int32_t *status,
                                     sspcg_stream stream) {
-  return solve_batched(plan, kOpQp, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status,
-                       stream, false);
+  if (!plan) return SSPCG_ERR_INVALID_ARG;
+  if (plan->nprob == 0) return SSPCG_OK;
+  sspcg_status s = check_solve_args(plan, kOpQp, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters,
+                                    relres, status);
+  if (s != SSPCG_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
+  plan->build_timed = false;
+  time_mark(plan, 1, st);
+  s = launch_sets(plan, {{&plan->sets[kSetQpAll], batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma,
+                                                               lambda, iters, relres, status)}},
+                  st);
+  time_mark(plan, 2, st);
+  return s;
 }
 
 sspcg_status sspcg_residual_qp_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
@@ -501,12 +668,69 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
                                     const float *qd, const float *rd, const float *gamma, float *D, float *E,
                                     float *PD, float *PE, float *lambda, int32_t *iters, double *relres,
                                     int32_t *status, sspcg_stream stream) {
-  sspcg_status s = sspcg_build_schur_batched(plan, A, B, qd, rd, D, E, stream);
+  if (!plan || kind < 0 || kind > 3) return SSPCG_ERR_INVALID_ARG;
+  if (plan->nprob == 0) return SSPCG_OK;
+  sspcg_status s = check_solve_args(plan, kOpQp, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters,
+                                    relres, status);
   if (s != SSPCG_OK) return s;
-  s = sspcg_build_precond_batched(plan, kind, D, E, PD, PE, status, stream);
-  if (s != SSPCG_OK) return s;
-  return solve_batched(plan, kOpQp, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status,
-                       stream, true);
+  if (!D || (plan->total_off > 0 && !E)) return SSPCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  time_mark(plan, 0, st);
+  // FP32 blocks for every problem (also returned to the caller), FP64 blocks for the FP64 subset
+  if ((s = sspcg_build_schur_batched(plan, A, B, qd, rd, D, E, stream)) != SSPCG_OK) return s;
+  if ((s = sspcg_build_precond_batched(plan, kind, D, E, PD, PE, status, stream)) != SSPCG_OK) return s;
+  if (plan->ntiny > 0) {
+    SSPCG_CUDA(launch_schur_build<double>(tiny_set(plan), plan->d_tknot_start, plan->tknots, A, B, qd, rd, plan->D64,
+                                          plan->E64, st, device_sms()));
+    SSPCG_CUDA(launch_precond_build<double>(tiny_set(plan), plan->d_tknot_start, plan->tknots, plan->d_toff_start,
+                                            plan->toff, (int)kind, plan->D64, plan->E64, plan->PD64, plan->PE64,
+                                            status, st, device_sms(), plan->t_offe));
+  }
+  plan->build_timed = true;
+  time_mark(plan, 1, st);
+  PcgArgs a32 = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
+  PcgArgs a64 = a32;
+  a64.ps = tiny_set(plan);
+  a64.PD = plan->PD64;
+  a64.PE = plan->PE64;
+  s = launch_sets(plan, {{&plan->sets[kSetQpMain], a32}, {&plan->sets[kSetTiny], a64}}, st);
+  time_mark(plan, 2, st);
+  return s;
+}
+
+sspcg_status sspcg_plan_capture_pipeline(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
+                                         const float *qd, const float *rd, const float *gamma, float *D, float *E,
+                                         float *PD, float *PE, float *lambda, int32_t *iters, double *relres,
+                                         int32_t *status, sspcg_stream stream) {
+  if (!plan || !stream) return SSPCG_ERR_INVALID_ARG;  // capture needs a non-default stream
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->graph) {
+    cudaGraphExecDestroy(plan->graph);
+    plan->graph = nullptr;
+  }
+  const bool timing = plan->timing;
+  plan->timing = false;
+  // run once uncaptured so that every kernel attribute is set before capture
+  sspcg_status s = sspcg_pipeline_batched(plan, kind, A, B, qd, rd, gamma, D, E, PD, PE, lambda, iters, relres,
+                                          status, stream);
+  if (s != SSPCG_OK) { plan->timing = timing; return s; }
+  SSPCG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  s = sspcg_pipeline_batched(plan, kind, A, B, qd, rd, gamma, D, E, PD, PE, lambda, iters, relres, status, stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  plan->timing = timing;
+  if (s != SSPCG_OK) { if (g) cudaGraphDestroy(g); return s; }
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaGraphInstantiate(&plan->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { plan->graph = nullptr; return cuda_fail(e); }
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_plan_launch(sspcg_plan *plan, sspcg_stream stream) {
+  if (!plan || !plan->graph) return SSPCG_ERR_INVALID_ARG;
+  SSPCG_CUDA(cudaGraphLaunch(plan->graph, (cudaStream_t)stream));
+  return SSPCG_OK;
 }
 
 sspcg_status sspcg_pipeline_host(sspcg_plan *plan, sspcg_precond kind, const float *A_host, const float *B_host,

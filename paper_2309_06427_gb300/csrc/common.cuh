@@ -14,7 +14,7 @@ enum SolveCode : int { kOk = 0, kMaxIter = 1, kBreakdown = 2, kNotSpd = 3, kNonF
 // Packed-batch descriptor of one problem: shape and float offsets into each
 // packed array kind (see SSPCG_ARRAY_* in sspcg.h).
 struct ProbDesc {
-  int32_t N, nx, nu, pad;
+  int32_t N, nx, nu, id;  // id: index of the problem in the caller's per-problem output arrays
   int64_t oA, oB, oq, orr, odiag, ooff, ovec;
 };
 

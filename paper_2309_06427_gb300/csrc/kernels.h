@@ -21,7 +21,7 @@ __host__ __device__ __forceinline__ int pad_ld(int x) { return x | 1; }
 // 16-byte aligned.  The same function sizes launches on the host and carves
 // on the device.
 struct PcgLayout {
-  int64_t p, r, w, v;               // vectors
+  int64_t p, r, w, x, v;            // vectors
   int64_t m0, m1, iq, ir, pd, pe;   // matrices (resident schedule only)
   int64_t total;
 };
@@ -33,6 +33,7 @@ __host__ __device__ inline PcgLayout pcg_layout(int op, bool resident, int N, in
   L.p = o; o += R4;
   L.r = o; o += R4;
   L.w = o; o += R4;
+  L.x = o; o += R4;
   L.v = o;
   if (op == kOpQp) o += round_up(n * nx + (int64_t)N * nu, 4);
   L.m0 = L.m1 = L.iq = L.ir = L.pd = L.pe = o;
@@ -60,11 +61,12 @@ struct PcgArgs {
   const int32_t *work;   // problem indices in processing order (device), or nullptr: identity
   int32_t nwork;
   int32_t *counter;      // work-queue counter (device, zeroed before launch), or nullptr: static
-  const float *A, *B, *qd, *rd;  // QP operator data (packed)
-  const float *D, *E;            // block operator data (packed)
-  const float *PD, *PE;
+  const float *A, *B, *qd, *rd;  // QP operator data (packed, FP32)
+  const float *D, *E;            // block operator data (packed, FP32)
+  const void *PD, *PE;           // preconditioner blocks in the working precision
   const float *gamma;
-  float *lambda;
+  void *lambda;                  // solution: float when lambda_f32, else the working precision
+  int32_t lambda_f32;
   int32_t *iters;
   double *relres;
   int32_t *status;       // in: nonzero skips the problem; out: solve code
@@ -74,17 +76,22 @@ struct PcgArgs {
 };
 
 // PCG launch for one nx; dispatches to the instantiation for that nx.
-cudaError_t launch_pcg(int nx, int op, int red, bool resident, const PcgArgs &a, int grid, int block, size_t smem,
-                       cudaStream_t st);
+// f64: the FP64 path (QP operator form only).
+cudaError_t launch_pcg(int nx, int op, int red, bool resident, bool f64, const PcgArgs &a, int grid, int block,
+                       size_t smem, cudaStream_t st);
 int pcg_max_smem_bytes();
 
+// Schur build and preconditioner assembly; Real = float (FP32 blocks) or
+// double (the FP64 path).
+template <typename Real>
 cudaError_t launch_schur_build(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots, const float *A,
-                               const float *B, const float *qd, const float *rd, float *D, float *E,
+                               const float *B, const float *qd, const float *rd, Real *D, Real *E,
                                cudaStream_t st, int sms);
+template <typename Real>
 cudaError_t launch_precond_build(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots,
-                                 const int64_t *off_start, int64_t total_off, int kind, const float *D,
-                                 const float *E, float *PD, float *PE, int32_t *status, cudaStream_t st, int sms,
-                                 int64_t off_floats);
+                                 const int64_t *off_start, int64_t total_off, int kind, const Real *D,
+                                 const Real *E, Real *PD, Real *PE, int32_t *status, cudaStream_t st, int sms,
+                                 int64_t off_elems);
 cudaError_t launch_residual_qp(const ProbSet &ps, const float *A, const float *B, const float *qd, const float *rd,
                                const float *gamma, const float *lambda, double *relres_true, cudaStream_t st);
 

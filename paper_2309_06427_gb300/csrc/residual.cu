@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kResThreads) residual_qp_kernel(ProbSet ps, co
     if (tid == 0) {
       double a = 0.0, b = 0.0;
       for (int w = 0; w < kResThreads / 32; ++w) { a += red[0][w]; b += red[1][w]; }
-      out[p] = b > 0.0 ? sqrt(a / b) : 0.0;
+      out[d.id] = b > 0.0 ? sqrt(a / b) : 0.0;
     }
     __syncthreads();
   }

@@ -22,6 +22,7 @@ SOLVE_OK, SOLVE_MAXITER, SOLVE_BREAKDOWN, SOLVE_NOT_SPD, SOLVE_NONFINITE = 0, 1,
 PRECOND = {"sym": 0, "add": 1, "bj": 2, "jacobi": 3}
 REDUCE = {"df": 0, "f32": 1, "f64": 2}
 SCHED = {"auto": 0, "resident": 1, "stream": 2}
+PRECISION = {"auto": 0, "f32": 1, "f64": 2}
 ARRAY_A, ARRAY_B, ARRAY_QD, ARRAY_RD, ARRAY_DIAG, ARRAY_OFF, ARRAY_VEC = range(7)
 NUM_ARRAYS = 7
 MAX_NX = 28
@@ -33,13 +34,15 @@ class SspcgError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("warm_start", ctypes.c_int32),
-                ("reduction", ctypes.c_int32), ("schedule", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+                ("reduction", ctypes.c_int32), ("schedule", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
 
 
-def options(tol=1e-6, max_iter=0, warm_start=0, reduction="df", schedule="auto", block_threads=0) -> Options:
-    return Options(float(tol), int(max_iter), int(warm_start), REDUCE[reduction] if isinstance(reduction, str)
-                   else int(reduction), SCHED[schedule] if isinstance(schedule, str) else int(schedule),
-                   int(block_threads))
+def options(tol=1e-6, max_iter=0, warm_start=0, reduction="df", schedule="auto", block_threads=0,
+            precision="auto") -> Options:
+    pick = lambda table, v: table[v] if isinstance(v, str) else int(v)
+    return Options(float(tol), int(max_iter), int(warm_start), pick(REDUCE, reduction), pick(SCHED, schedule),
+                   int(block_threads), pick(PRECISION, precision))
 
 
 _lib = None
@@ -60,11 +63,19 @@ def lib() -> ctypes.CDLL:
             "sspcg_solve_qp": [_I32, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(Options),
                                _VP, _VP, _VP, _VP],
             "sspcg_residual_qp": [_I32, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+            "sspcg_build_schur_f64": [_I32, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+            "sspcg_build_precond_f64": [_I32, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP],
+            "sspcg_solve_qp_f64": [_I32, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(Options),
+                                   _VP, _VP, _VP, _VP],
             "sspcg_plan_create": [ctypes.POINTER(_VP), _I32, _VP, _VP, _VP, ctypes.POINTER(Options)],
             "sspcg_plan_destroy": [_VP],
             "sspcg_plan_sizes": [_VP, _VP],
             "sspcg_plan_offsets": [_VP, _I32, _VP],
             "sspcg_plan_stats": [_VP, _VP],
+            "sspcg_plan_set_timing": [_VP, _I32],
+            "sspcg_plan_timings": [_VP, _VP],
+            "sspcg_plan_capture_pipeline": [_VP, _I32] + [_VP] * 14,
+            "sspcg_plan_launch": [_VP, _VP],
             "sspcg_build_schur_batched": [_VP] * 8,
             "sspcg_build_precond_batched": [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP],
             "sspcg_solve_batched": [_VP] * 11,
@@ -138,6 +149,24 @@ def sspcg_solve_qp(N, nx, nu, A, B, qd, rd, PD, PE, gamma, lam, opts: Options, i
                                 _stream(stream)), "sspcg_solve_qp")
 
 
+def sspcg_build_schur_f64(N, nx, nu, A, B, qd, rd, D, E, stream=None):
+    _check(lib().sspcg_build_schur_f64(N, nx, nu, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(D), _ptr(E),
+                                       _stream(stream)), "sspcg_build_schur_f64")
+
+
+def sspcg_build_precond_f64(N, nx, kind, D, E, PD, PE, status, stream=None):
+    k = PRECOND[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().sspcg_build_precond_f64(N, nx, k, _ptr(D), _ptr(E), _ptr(PD), _ptr(PE), _ptr(status),
+                                         _stream(stream)), "sspcg_build_precond_f64")
+
+
+def sspcg_solve_qp_f64(N, nx, nu, A, B, qd, rd, PD, PE, gamma, lam, opts: Options, iters, relres, status,
+                       stream=None):
+    _check(lib().sspcg_solve_qp_f64(N, nx, nu, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(PD), _ptr(PE),
+                                    _ptr(gamma), _ptr(lam), ctypes.byref(opts), _ptr(iters), _ptr(relres),
+                                    _ptr(status), _stream(stream)), "sspcg_solve_qp_f64")
+
+
 def sspcg_residual_qp(N, nx, nu, A, B, qd, rd, gamma, lam, relres_true, stream=None):
     _check(lib().sspcg_residual_qp(N, nx, nu, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(gamma), _ptr(lam),
                                    _ptr(relres_true), _stream(stream)), "sspcg_residual_qp")
@@ -202,10 +231,35 @@ def sspcg_plan_create(N, nx, nu, opts: Options) -> Plan:
 
 
 def sspcg_plan_stats(plan: Plan) -> Dict[str, int]:
-    out = np.zeros(6, dtype=np.int64)
+    out = np.zeros(8, dtype=np.int64)
     _check(lib().sspcg_plan_stats(plan.handle, out.ctypes.data), "sspcg_plan_stats")
-    keys = ["qp_launches", "qp_resident", "qp_stream", "block_launches", "block_resident", "block_stream"]
+    keys = ["pipeline_launches", "pipeline_resident", "pipeline_stream", "pipeline_f64", "solve_qp_launches",
+            "solve_block_launches", "solve_qp_resident", "solve_qp_stream"]
     return {k: int(v) for k, v in zip(keys, out)}
+
+
+def sspcg_plan_set_timing(plan: Plan, enable: bool = True):
+    _check(lib().sspcg_plan_set_timing(plan.handle, int(bool(enable))), "sspcg_plan_set_timing")
+
+
+def sspcg_plan_timings(plan: Plan):
+    """(build_ms, pcg_ms) of the plan's last pipeline or solve call."""
+    out = np.zeros(2, dtype=np.float32)
+    _check(lib().sspcg_plan_timings(plan.handle, out.ctypes.data), "sspcg_plan_timings")
+    return float(out[0]), float(out[1])
+
+
+def sspcg_plan_capture_pipeline(plan: Plan, kind, A, B, qd, rd, gamma, D, E, PD, PE, lam, iters, relres, status,
+                                stream):
+    k = PRECOND[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().sspcg_plan_capture_pipeline(plan.handle, k, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(gamma),
+                                             _ptr(D), _ptr(E), _ptr(PD), _ptr(PE), _ptr(lam), _ptr(iters),
+                                             _ptr(relres), _ptr(status), _stream(stream)),
+           "sspcg_plan_capture_pipeline")
+
+
+def sspcg_plan_launch(plan: Plan, stream=None):
+    _check(lib().sspcg_plan_launch(plan.handle, _stream(stream)), "sspcg_plan_launch")
 
 
 plan_stats = sspcg_plan_stats
@@ -289,6 +343,11 @@ class Batch:
         d = self.dev
         sspcg_pipeline_batched(self.plan, kind, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], self.D, self.E, self.PD,
                                self.PE, self.lam, self.iters, self.relres, self.status, stream)
+
+    def capture(self, kind, stream):
+        d = self.dev
+        sspcg_plan_capture_pipeline(self.plan, kind, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], self.D, self.E,
+                                    self.PD, self.PE, self.lam, self.iters, self.relres, self.status, stream)
 
     def lambdas(self) -> List[np.ndarray]:
         return self.plan.unpack(ARRAY_VEC, self.lam, [p.gamma.shape for p in self.probs])

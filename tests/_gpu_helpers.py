@@ -10,6 +10,21 @@ from paper_2309_06427_gb300 import sspcg
 # iteration counts within one.
 LAMBDA_RTOL = 1e-5
 ITER_TOL = 1
+# Problems of at most this many unknowns take the FP64 path in the pipeline
+# (same threshold as the library's SSPCG_PRECISION_AUTO).
+TINY_UNKNOWNS = 192
+
+
+def is_tiny(p):
+    return p.n * p.nx <= TINY_UNKNOWNS
+
+
+def iters_ok(it_gpu, it_oracle, fp32_tiny=False):
+    """Iteration parity.  FP32 on tiny problems cannot reproduce the finite termination of
+    FP64 CG on the clustered spectrum (Thm. 4.2): there it may take more iterations, bounded."""
+    if fp32_tiny:
+        return it_oracle - ITER_TOL <= it_gpu <= 2 * it_oracle + 2
+    return abs(it_gpu - it_oracle) <= ITER_TOL
 
 
 def dev(a, dtype=torch.float32):
@@ -56,6 +71,30 @@ def gpu_solve_qp(p, kind="sym", tol=1e-6, lam0=None, **kw):
     sspcg.sspcg_solve_qp(p.N, p.nx, p.nu, A, B, qd, rd, PD, PE, g, lam, opts, it, rr, st)
     torch.cuda.synchronize()
     return lam.cpu().numpy()[:p.gamma.size].reshape(p.gamma.shape), int(it.item()), float(rr.item()), int(st.item())
+
+
+def gpu_solve_qp_f64(p, kind="sym", tol=1e-6, **kw):
+    """Whole single-problem path on the GPU in FP64: returns (lambda, iters, relres, status)."""
+    n, m = p.n, p.nx
+    A, B, qd, rd = dev(p.A), dev(p.B), dev(p.qd), dev(p.rd)
+    D = torch.zeros(max(n * m * m, 2), dtype=torch.float64, device="cuda")
+    E = torch.zeros(max(p.N * m * m, 2), dtype=torch.float64, device="cuda")
+    PD, PE = torch.zeros_like(D), torch.zeros_like(E)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sspcg.sspcg_build_schur_f64(p.N, m, p.nu, A, B, qd, rd, D, E)
+    sspcg.sspcg_build_precond_f64(p.N, m, kind, D, E, PD, PE, st)
+    g = dev(p.gamma)
+    lam = torch.zeros(max(n * m, 2), dtype=torch.float64, device="cuda")
+    it = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rr = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sspcg.sspcg_solve_qp_f64(p.N, m, p.nu, A, B, qd, rd, PD, PE, g, lam, sspcg.options(tol=tol, **kw), it, rr, st)
+    torch.cuda.synchronize()
+    return lam.cpu().numpy()[:p.gamma.size].reshape(p.gamma.shape), int(it.item()), float(rr.item()), int(st.item())
+
+
+def gpu_solve_auto(p, kind="sym", tol=1e-6, **kw):
+    """The precision the batched pipeline uses for this problem (FP64 when tiny)."""
+    return gpu_solve_qp_f64(p, kind, tol, **kw) if is_tiny(p) else gpu_solve_qp(p, kind, tol, **kw)
 
 
 def blocks_to_oracle(p, D, E):
