@@ -70,10 +70,6 @@ int red_mode(int32_t r) {
   return kRedDf;
 }
 
-int64_t pcg_smem_bytes(int op, bool res, int N, int nx, int nu, bool f64 = false) {
-  return pcg_layout(op, res, N, nx, nu).total * (int64_t)(f64 ? sizeof(double) : sizeof(float));
-}
-
 int64_t smem_budget() { return (int64_t)max_smem_optin() - kPcgStaticSmem; }  // bytes of dynamic smem
 
 // Threads per CTA for a problem with R rows: about two rows per thread.
@@ -82,14 +78,16 @@ int auto_block(int64_t rows) {
   return (int)std::min<int64_t>(256, std::max<int64_t>(64, t));
 }
 
-// Choose residency for a problem; returns false when even the streaming
-// layout does not fit.
-bool choose_resident(int op, int sched, int N, int nx, int nu, bool *resident, bool f64 = false) {
-  const int64_t budget = smem_budget();
-  const bool fits_res = pcg_smem_bytes(op, true, N, nx, nu, f64) <= budget;
-  const bool fits_str = pcg_smem_bytes(op, false, N, nx, nu, f64) <= budget;
-  if (!fits_str) return false;
-  *resident = (sched != SSPCG_SCHED_STREAM) && fits_res;
+// Staged block rows K and dynamic shared memory (bytes) of a PCG problem
+// under a schedule; false when even the vectors do not fit.
+bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int *K, int64_t *bytes) {
+  const int64_t esz = f64 ? sizeof(double) : sizeof(float);
+  const int64_t budget = smem_budget() / esz;
+  int k = pcg_max_resident(op, N, nx, nu, budget);
+  if (k < 0) return false;
+  if (sched == SSPCG_SCHED_STREAM) k = 0;
+  *K = k;
+  *bytes = pcg_layout(op, k, N, nx, nu).total * esz;
   return true;
 }
 
@@ -143,8 +141,18 @@ struct GroupSet {
 
 enum { kSetQpAll = 0, kSetBlockAll = 1, kSetQpMain = 2, kSetTiny = 3, kNumSets = 4 };
 
+// Problems of one nx, for the thread-per-knot kernels.
+struct NxGroup {
+  int nx = 0;
+  int32_t nprob = 0;
+  int64_t knots = 0;
+  ProbDesc *d_desc = nullptr;
+  int64_t *d_knot_start = nullptr;
+};
+
 struct sspcg_plan {
   int32_t nprob = 0;
+  std::vector<NxGroup> nxg_all, nxg_tiny;
   sspcg_options opts{};
   std::vector<ProbDesc> hdesc;
   std::vector<int64_t> offsets[SSPCG_NUM_ARRAYS];
@@ -189,6 +197,11 @@ void plan_free(sspcg_plan *p) {
                     (void *)p->PD64, (void *)p->PE64, (void *)p->d_work, (void *)p->d_counters, (void *)p->hbuf,
                     (void *)p->hint, (void *)p->hdbl})
     cudaFree(ptr);
+  for (auto *v : {&p->nxg_all, &p->nxg_tiny})
+    for (NxGroup &g : *v) {
+      cudaFree(g.d_desc);
+      cudaFree(g.d_knot_start);
+    }
   for (auto s : p->side) cudaStreamDestroy(s);
   for (auto e : p->ev) cudaEventDestroy(e);
   for (auto e : p->tev)
@@ -201,11 +214,12 @@ void plan_free(sspcg_plan *p) {
 sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDesc> &descs,
                          const std::vector<int32_t> &members, std::vector<int32_t> &work_host, int32_t &pos) {
   std::vector<std::vector<int32_t>> buckets(2 * (kMaxNx + 1));
+  std::vector<int64_t> bytes(descs.size(), 0);
   for (int32_t i : members) {
     const ProbDesc &d = descs[i];
-    bool res = false;
-    if (!choose_resident(set.op, p->opts.schedule, d.N, d.nx, d.nu, &res, set.f64)) return SSPCG_ERR_UNSUPPORTED;
-    buckets[2 * d.nx + (res ? 1 : 0)].push_back(i);
+    int K = 0;
+    if (!pcg_fit(set.op, p->opts.schedule, d.N, d.nx, d.nu, set.f64, &K, &bytes[i])) return SSPCG_ERR_UNSUPPORTED;
+    buckets[2 * d.nx + (K == d.N + 1 ? 1 : 0)].push_back(i);  // fully resident or not
   }
   for (int nx = 1; nx <= kMaxNx; ++nx) {
     for (int r = 0; r < 2; ++r) {
@@ -220,7 +234,7 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
       for (int32_t i : b) {
         const ProbDesc &d = descs[i];
         maxrows = std::max<int64_t>(maxrows, (int64_t)(d.N + 1) * d.nx);
-        maxsmem = std::max<int64_t>(maxsmem, pcg_smem_bytes(set.op, g.resident, d.N, d.nx, d.nu, set.f64));
+        maxsmem = std::max<int64_t>(maxsmem, bytes[i]);
       }
       g.block = p->opts.block_threads > 0 ? p->opts.block_threads : auto_block(maxrows);
       g.smem = (size_t)maxsmem;
@@ -245,6 +259,7 @@ PcgArgs make_args(const sspcg_options *o) {
   a.max_iter = o->max_iter;
   a.warm = o->warm_start;
   a.lambda_f32 = 1;
+  a.max_resident = o->schedule == SSPCG_SCHED_STREAM ? 0 : (1 << 30);
   return a;
 }
 
@@ -279,7 +294,7 @@ sspcg_status launch_sets(sspcg_plan *p, std::initializer_list<SetLaunch> list, c
     a.counter = p->d_counters + g.counter_index;
     cudaStream_t s = i == 0 ? st : p->side[i - 1];
     const int red = g.f64 ? kRedF64 : red_mode(p->opts.reduction);
-    SSPCG_CUDA(launch_pcg(g.nx, all[i].op, red, g.resident, g.f64, a, g.grid, g.block, g.smem, s));
+    SSPCG_CUDA(launch_pcg(g.nx, all[i].op, red, g.f64, a, g.grid, g.block, g.smem, s));
   }
   for (size_t i = 1; i < ng; ++i) {
     SSPCG_CUDA(cudaEventRecord(p->ev[i], p->side[i - 1]));
@@ -294,6 +309,30 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
   cudaError_t e = cudaMalloc(dst, sizeof(T) * src.size());
   if (e != cudaSuccess) return e;
   return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+// Split ``members`` of ``descs`` by nx into device descriptor subsets with knot prefixes.
+cudaError_t make_nx_groups(const std::vector<ProbDesc> &descs, const std::vector<int32_t> &members,
+                           std::vector<NxGroup> &out) {
+  for (int nx = 1; nx <= kMaxNx; ++nx) {
+    std::vector<ProbDesc> sub;
+    std::vector<int64_t> ks(1, 0);
+    for (int32_t i : members)
+      if (descs[i].nx == nx) {
+        sub.push_back(descs[i]);
+        ks.push_back(ks.back() + descs[i].N + 1);
+      }
+    if (sub.empty()) continue;
+    NxGroup g;
+    g.nx = nx;
+    g.nprob = (int32_t)sub.size();
+    g.knots = ks.back();
+    out.push_back(g);  // pushed first so that plan_free releases partial uploads
+    cudaError_t e = upload(&out.back().d_desc, sub);
+    if (e == cudaSuccess) e = upload(&out.back().d_knot_start, ks);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 void time_mark(sspcg_plan *p, int i, cudaStream_t st) {
@@ -331,8 +370,8 @@ sspcg_status sspcg_build_precond_f64(int32_t N, int32_t nx, sspcg_precond kind, 
   cudaStream_t st = (cudaStream_t)stream;
   ProbSet ps{nullptr, single_desc(N, nx, 0), 1};
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-  SSPCG_CUDA(launch_precond_build<double>(ps, nullptr, N + 1, nullptr, N, (int)kind, D, E, PD, PE, status, st,
-                                          device_sms(), (int64_t)N * nx * nx));
+  SSPCG_CUDA(launch_precond_inv<double>(ps, nullptr, N + 1, nx, (int)kind, D, PD, status, st));
+  SSPCG_CUDA(launch_precond_off<double>(ps, nullptr, N, (int)kind, E, PD, PE, st, device_sms(), (int64_t)N * nx * nx));
   return SSPCG_OK;
 }
 
@@ -343,8 +382,8 @@ sspcg_status sspcg_build_precond(int32_t N, int32_t nx, sspcg_precond kind, cons
   cudaStream_t st = (cudaStream_t)stream;
   ProbSet ps{nullptr, single_desc(N, nx, 0), 1};
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-  SSPCG_CUDA(launch_precond_build<float>(ps, nullptr, N + 1, nullptr, N, (int)kind, D, E, PD, PE, status, st,
-                                         device_sms(), (int64_t)N * nx * nx));
+  SSPCG_CUDA(launch_precond_inv<float>(ps, nullptr, N + 1, nx, (int)kind, D, PD, status, st));
+  SSPCG_CUDA(launch_precond_off<float>(ps, nullptr, N, (int)kind, E, PD, PE, st, device_sms(), (int64_t)N * nx * nx));
   return SSPCG_OK;
 }
 
@@ -358,8 +397,9 @@ static sspcg_status solve_single(int op, bool f64, int32_t N, int32_t nx, int32_
   if (!PD || !gamma || !lambda || !iters || !relres || !status || (N > 0 && !PE)) return SSPCG_ERR_INVALID_ARG;
   if (op == kOpQp && (!qd || (N > 0 && (!A || !rd || (nu > 0 && !B))))) return SSPCG_ERR_INVALID_ARG;
   if (op == kOpBlock && (!D || (N > 0 && !E))) return SSPCG_ERR_INVALID_ARG;
-  bool res = false;
-  if (!choose_resident(op, opts->schedule, N, nx, nu, &res, f64)) return SSPCG_ERR_UNSUPPORTED;
+  int K = 0;
+  int64_t bytes = 0;
+  if (!pcg_fit(op, opts->schedule, N, nx, nu, f64, &K, &bytes)) return SSPCG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   PcgArgs a = make_args(opts);
   a.ps = ProbSet{nullptr, single_desc(N, nx, nu), 1};
@@ -369,8 +409,7 @@ static sspcg_status solve_single(int op, bool f64, int32_t N, int32_t nx, int32_
   a.lambda_f32 = f64 ? 0 : 1;
   const int block = opts->block_threads > 0 ? opts->block_threads : auto_block((int64_t)(N + 1) * nx);
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-  SSPCG_CUDA(launch_pcg(nx, op, f64 ? kRedF64 : red_mode(opts->reduction), res, f64, a, 1, block,
-                        (size_t)pcg_smem_bytes(op, res, N, nx, nu, f64), st));
+  SSPCG_CUDA(launch_pcg(nx, op, f64 ? kRedF64 : red_mode(opts->reduction), f64, a, 1, block, (size_t)bytes, st));
   return SSPCG_OK;
 }
 
@@ -473,7 +512,11 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     if ((e = upload(&p->d_desc, p->hdesc)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = upload(&p->d_knot_start, knot_start)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = upload(&p->d_off_start, off_start)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = make_nx_groups(p->hdesc, all, p->nxg_all)) != cudaSuccess) return fail(cuda_fail(e));
     if (p->ntiny > 0) {
+      std::vector<int32_t> tl(p->ntiny);
+      std::iota(tl.begin(), tl.end(), 0);
+      if ((e = make_nx_groups(p->tdesc, tl, p->nxg_tiny)) != cudaSuccess) return fail(cuda_fail(e));
       if ((e = upload(&p->d_tdesc, p->tdesc)) != cudaSuccess) return fail(cuda_fail(e));
       if ((e = upload(&p->d_tknot_start, tknot)) != cudaSuccess) return fail(cuda_fail(e));
       if ((e = upload(&p->d_toff_start, toff)) != cudaSuccess) return fail(cuda_fail(e));
@@ -587,9 +630,11 @@ sspcg_status sspcg_build_precond_batched(sspcg_plan *plan, sspcg_precond kind, c
   if (!D || !PD || !status || (plan->total_off > 0 && (!E || !PE))) return SSPCG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
-  SSPCG_CUDA(launch_precond_build<float>(plan_set(plan), plan->d_knot_start, plan->total_knots, plan->d_off_start,
-                                         plan->total_off, (int)kind, D, E, PD, PE, status, st, device_sms(),
-                                         plan->sizes[SSPCG_ARRAY_OFF]));
+  for (const NxGroup &g : plan->nxg_all)
+    SSPCG_CUDA(launch_precond_inv<float>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_knot_start, g.knots, g.nx,
+                                         (int)kind, D, PD, status, st));
+  SSPCG_CUDA(launch_precond_off<float>(plan_set(plan), plan->d_off_start, plan->total_off, (int)kind, E, PD, PE, st,
+                                       device_sms(), plan->sizes[SSPCG_ARRAY_OFF]));
   return SSPCG_OK;
 }
 
@@ -682,9 +727,11 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
   if (plan->ntiny > 0) {
     SSPCG_CUDA(launch_schur_build<double>(tiny_set(plan), plan->d_tknot_start, plan->tknots, A, B, qd, rd, plan->D64,
                                           plan->E64, st, device_sms()));
-    SSPCG_CUDA(launch_precond_build<double>(tiny_set(plan), plan->d_tknot_start, plan->tknots, plan->d_toff_start,
-                                            plan->toff, (int)kind, plan->D64, plan->E64, plan->PD64, plan->PE64,
-                                            status, st, device_sms(), plan->t_offe));
+    for (const NxGroup &g : plan->nxg_tiny)
+      SSPCG_CUDA(launch_precond_inv<double>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_knot_start, g.knots, g.nx,
+                                            (int)kind, plan->D64, plan->PD64, status, st));
+    SSPCG_CUDA(launch_precond_off<double>(tiny_set(plan), plan->d_toff_start, plan->toff, (int)kind, plan->E64,
+                                          plan->PD64, plan->PE64, st, device_sms(), plan->t_offe));
   }
   plan->build_timed = true;
   time_mark(plan, 1, st);

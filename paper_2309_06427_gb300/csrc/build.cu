@@ -1,6 +1,8 @@
 // Schur-block build (Sec. II-A) and preconditioner assembly (Eq. stair_inv,
 // Sec. III, Sec. IV, Eq. jacobi).  One warp per knot; the batch is a flat
 // list of knots, each warp finding its problem by binary search.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -83,12 +85,18 @@ __global__ void __launch_bounds__(kBuildWarps * 32) schur_build_kernel(ProbSet p
 }
 
 // ---------------------------------------------------------------------------
-// K2a: PD_k = D_k^-1.  FP64 LDL^T of the SPD block (no square roots), then
-// D^-1 = L^-T diag(1/d) L^-1.  Lane i owns row i (nx <= 28 < 32).
-// Reciprocals start from the FP32 reciprocal and take two Newton steps in
-// FP64 (each doubles the correct bits: 2^-23 -> 2^-46 -> below 2^-53).
-// Jacobi: PD_k = diag(1 / D_k(i,i)).
-// Shared memory per warp: M (nx*nx doubles), W (nx*nx doubles), invd (nx doubles).
+// K2a: PD_k = D_k^-1 in FP64, one thread per knot (all knots of a launch have
+// the same nx).  GB300 issues FP64 at about 1/64 of the FP32 rate and a warp
+// instruction costs the same with any number of active lanes, so every lane
+// works on a knot of its own.  Per thread, in shared memory: the lower
+// triangle of D_k (row stride nx, odd total stride per thread for
+// conflict-free 8-byte accesses).
+//   LDL^T, right-looking, rows updated from the bottom so that column j stays
+//   unscaled until its row is done:            nx^3/6 FMA
+//   L^-1 in place (unit lower), column by column:  nx^3/6 FMA
+//   D^-1(i,j) = sum_{t>=i} W(t,i) (1/d_t) W(t,j), i >= j:  nx^3/6 FMA
+// Reciprocals: FP32 reciprocal refined by two FP64 Newton steps
+// (2^-23 -> 2^-46 -> below 2^-53).  Jacobi: PD_k = diag(1 / D_k(i,i)).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double rcp_f64(double x) {
   double y = (double)(1.0f / (float)x);
@@ -97,91 +105,68 @@ __device__ __forceinline__ double rcp_f64(double x) {
   return y;
 }
 
+__host__ __device__ __forceinline__ int inv_stride(int nx) { return (nx * nx) | 1; }
+
 template <typename Real>
-__global__ void __launch_bounds__(kBuildWarps * 32) precond_diag_kernel(ProbSet ps, const int64_t *knot_start,
-                                                                       int64_t total_knots, int kind,
-                                                                       const Real *__restrict__ D, Real *PD,
-                                                                       int32_t *status) {
+__global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int64_t *knot_start, int64_t total_knots,
+                                                         int nx, int kind, const Real *__restrict__ D, Real *PD,
+                                                         int32_t *status) {
   extern __shared__ double dsm[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int per_warp = 2 * kMaxNx * kMaxNx + kMaxNx;
-  double *M = dsm + wid * per_warp;
-  double *W = M + kMaxNx * kMaxNx;
-  double *invd = W + kMaxNx * kMaxNx;
-  for (int64_t g = (int64_t)blockIdx.x * kBuildWarps + wid; g < total_knots; g += (int64_t)gridDim.x * kBuildWarps) {
-    const int p = knot_start ? find_problem(knot_start, ps.nprob, g) : 0;
-    const ProbDesc d = ps.get(p);
-    const int k = (int)(g - (knot_start ? knot_start[p] : 0));
-    const int nx = d.nx, nn = nx * nx;
-    const Real *Dk = D + d.odiag + (int64_t)k * nn;
-    Real *PDk = PD + d.odiag + (int64_t)k * nn;
-    if (kind == 3) {  // Jacobi
-      bool bad = false;
-      for (int e = lane; e < nn; e += 32) {
-        const int i = e / nx, j = e - i * nx;
-        Real v = Real(0);
-        if (i == j) {
-          const Real s = Dk[e];
-          bad |= !(s > Real(0)) || !isfinite(s);
-          v = Real(1) / s;
-        }
-        PDk[e] = v;
-      }
-      if (__any_sync(0xffffffffu, bad) && lane == 0) status[d.id] = kNotSpd;
-      continue;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total_knots) return;
+  const int p = knot_start ? find_problem(knot_start, ps.nprob, g) : 0;
+  const ProbDesc d = ps.get(p);
+  const int k = (int)(g - (knot_start ? knot_start[p] : 0));
+  const int nn = nx * nx;
+  const Real *Dk = D + d.odiag + (int64_t)k * nn;
+  Real *PDk = PD + d.odiag + (int64_t)k * nn;
+  if (kind == 3) {  // Jacobi
+    bool bad = false;
+    for (int e = 0; e < nn; ++e) PDk[e] = Real(0);
+    for (int i = 0; i < nx; ++i) {
+      const Real s = Dk[i * nx + i];
+      bad |= !(s > Real(0)) || !isfinite(s);
+      PDk[i * nx + i] = Real(1) / s;
     }
-    for (int e = lane; e < nn; e += 32) M[e] = (double)Dk[e];
-    __syncwarp();
-    // LDL^T, right-looking.  After step j: invd[j] = 1/d_j, M(i, j) = L(i, j) for i > j.
-    bool ok = true;
-    for (int j = 0; j < nx; ++j) {
-      const double djj = M[j * nx + j];
-      if (!(djj > 0.0) || !isfinite(djj)) { ok = false; break; }
-      const double inv = rcp_f64(djj);
-      double uij = 0.0;  // unscaled column value M(i, j) of this lane's row
-      if (lane > j && lane < nx) uij = M[lane * nx + j];
-      __syncwarp();
-      if (lane > j && lane < nx) {
-        const double lij = uij * inv;
-        // trailing update of row `lane`, columns j+1..lane: M(i,c) -= L(i,j) * u(c,j)
-        for (int c = j + 1; c <= lane; ++c) M[lane * nx + c] -= lij * M[c * nx + j];
-      }
-      __syncwarp();
-      if (lane > j && lane < nx) M[lane * nx + j] = uij * inv;
-      if (lane == 0) invd[j] = inv;
-      __syncwarp();
+    if (bad) status[d.id] = kNotSpd;
+    return;
+  }
+  double *M = dsm + (int64_t)threadIdx.x * inv_stride(nx);
+  for (int i = 0; i < nx; ++i)
+    for (int c = 0; c <= i; ++c) M[i * nx + c] = (double)Dk[i * nx + c];
+  // LDL^T: after step j, M(j,j) = 1/d_j and M(i,j) = L(i,j) for i > j.
+  for (int j = 0; j < nx; ++j) {
+    const double djj = M[j * nx + j];
+    if (!(djj > 0.0) || !isfinite(djj)) {
+      status[d.id] = kNotSpd;
+      for (int e = 0; e < nn; ++e) PDk[e] = Real(0);
+      return;
     }
-    if (!ok) {
-      if (lane == 0) status[d.id] = kNotSpd;
-      for (int e = lane; e < nn; e += 32) PDk[e] = Real(0);
-      __syncwarp();
-      continue;
+    const double inv = rcp_f64(djj);
+    for (int i = nx - 1; i > j; --i) {
+      const double lij = M[i * nx + j] * inv;
+      for (int c = j + 1; c <= i; ++c) M[i * nx + c] = fma(-lij, M[c * nx + j], M[i * nx + c]);
+      M[i * nx + j] = lij;
     }
-    // W = L^-1 (unit lower): lane c computes column c by forward substitution.
-    if (lane < nx) {
-      const int c = lane;
-      for (int i = 0; i < nx; ++i) {
-        double v = 0.0;
-        if (i == c) v = 1.0;
-        else if (i > c) {
-          for (int t = c; t < i; ++t) v -= M[i * nx + t] * W[t * nx + c];
-        }
-        W[i * nx + c] = v;
-      }
+    M[j * nx + j] = inv;
+  }
+  // W = L^-1 (unit lower) in place, column by column.
+  for (int j = 0; j + 1 < nx; ++j) {
+    for (int i = j + 1; i < nx; ++i) {
+      double s = M[i * nx + j];
+      for (int t = j + 1; t < i; ++t) s = fma(M[i * nx + t], M[t * nx + j], s);
+      M[i * nx + j] = -s;
     }
-    __syncwarp();
-    // D^-1(i, j) = sum_{t >= max(i,j)} W(t, i) W(t, j) / d_t; lane i computes j >= i and mirrors.
-    if (lane < nx) {
-      const int i = lane;
-      for (int j = i; j < nx; ++j) {
-        double s = 0.0;
-        for (int t = j; t < nx; ++t) s += W[t * nx + i] * W[t * nx + j] * invd[t];
-        const Real f = (Real)s;
-        PDk[i * nx + j] = f;
-        PDk[j * nx + i] = f;
-      }
+  }
+  // D^-1 = W^T diag(1/d) W, lower triangle, mirrored.
+  for (int i = 0; i < nx; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = M[i * nx + i] * (i == j ? 1.0 : M[i * nx + j]);
+      for (int t = i + 1; t < nx; ++t) s = fma(M[t * nx + i] * M[t * nx + t], M[t * nx + j], s);
+      const Real f = (Real)s;
+      PDk[i * nx + j] = f;
+      PDk[j * nx + i] = f;
     }
-    __syncwarp();
   }
 }
 
@@ -263,30 +248,41 @@ cudaError_t launch_schur_build(const ProbSet &ps, const int64_t *knot_start, int
 }
 
 template <typename Real>
-cudaError_t launch_precond_build(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots,
-                                 const int64_t *off_start, int64_t total_off, int kind, const Real *D,
-                                 const Real *E, Real *PD, Real *PE, int32_t *status, cudaStream_t st, int sms,
-                                 int64_t off_elems) {
+cudaError_t launch_precond_inv(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots, int nx, int kind,
+                               const Real *D, Real *PD, int32_t *status, cudaStream_t st) {
   if (total_knots == 0) return cudaSuccess;
-  const size_t smem_d = sizeof(double) * kBuildWarps * (2 * kMaxNx * kMaxNx + kMaxNx);
+  static int attr_set = 0;
+  const int per_thread = inv_stride(nx) * (int)sizeof(double);
+  int threads = (int)std::min<int64_t>(256, (200 * 1024 / per_thread) / 32 * 32);
+  if (threads < 32) threads = 32;
+  if (kind == 3) threads = 256;
+  const size_t smem = kind == 3 ? 0 : (size_t)threads * per_thread;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(precond_inv_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         210 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = 1;
+  }
+  const int64_t grid = cdiv(total_knots, threads);
+  precond_inv_kernel<Real><<<(unsigned)grid, threads, smem, st>>>(ps, knot_start, total_knots, nx, kind, D, PD,
+                                                                   status);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_precond_off(const ProbSet &ps, const int64_t *off_start, int64_t total_off, int kind,
+                               const Real *E, const Real *PD, Real *PE, cudaStream_t st, int sms, int64_t off_elems) {
+  if (total_off == 0) return cudaSuccess;
+  if (kind == 2 || kind == 3) {  // block-Jacobi, Jacobi: no off-diagonal blocks
+    return cudaMemsetAsync(PE, 0, sizeof(Real) * off_elems, st);
+  }
   const size_t smem_o = sizeof(Real) * kBuildWarps * (4 * kMaxNx * kMaxNx);
   static bool attr = false;
   if (!attr) {
     cudaError_t e =
-        cudaFuncSetAttribute(precond_diag_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(precond_off_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_o);
+        cudaFuncSetAttribute(precond_off_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_o);
     if (e != cudaSuccess) return e;
     attr = true;
-  }
-  precond_diag_kernel<Real><<<build_grid(total_knots, sms), kBuildWarps * 32, smem_d, st>>>(ps, knot_start,
-                                                                                             total_knots, kind, D, PD,
-                                                                                             status);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
-  if (total_off == 0) return cudaSuccess;
-  if (kind == 2 || kind == 3) {  // block-Jacobi, Jacobi: no off-diagonal blocks
-    return cudaMemsetAsync(PE, 0, sizeof(Real) * off_elems, st);
   }
   const Real c = (kind == 0) ? Real(1) : Real(0.5);
   precond_off_kernel<Real><<<build_grid(total_off, sms), kBuildWarps * 32, smem_o, st>>>(ps, off_start, total_off, c,
@@ -299,11 +295,13 @@ template cudaError_t launch_schur_build<float>(const ProbSet &, const int64_t *,
 template cudaError_t launch_schur_build<double>(const ProbSet &, const int64_t *, int64_t, const float *,
                                                 const float *, const float *, const float *, double *, double *,
                                                 cudaStream_t, int);
-template cudaError_t launch_precond_build<float>(const ProbSet &, const int64_t *, int64_t, const int64_t *, int64_t,
-                                                 int, const float *, const float *, float *, float *, int32_t *,
-                                                 cudaStream_t, int, int64_t);
-template cudaError_t launch_precond_build<double>(const ProbSet &, const int64_t *, int64_t, const int64_t *,
-                                                  int64_t, int, const double *, const double *, double *, double *,
-                                                  int32_t *, cudaStream_t, int, int64_t);
+template cudaError_t launch_precond_inv<float>(const ProbSet &, const int64_t *, int64_t, int, int, const float *,
+                                               float *, int32_t *, cudaStream_t);
+template cudaError_t launch_precond_inv<double>(const ProbSet &, const int64_t *, int64_t, int, int, const double *,
+                                                double *, int32_t *, cudaStream_t);
+template cudaError_t launch_precond_off<float>(const ProbSet &, const int64_t *, int64_t, int, const float *,
+                                               const float *, float *, cudaStream_t, int, int64_t);
+template cudaError_t launch_precond_off<double>(const ProbSet &, const int64_t *, int64_t, int, const double *,
+                                                const double *, double *, cudaStream_t, int, int64_t);
 
 }  // namespace sspcg

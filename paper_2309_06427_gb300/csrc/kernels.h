@@ -17,18 +17,23 @@ enum RedMode : int { kRedF32 = 0, kRedDf = 1, kRedF64 = 2 };
 // 32 consecutive rows touch 32 distinct banks.
 __host__ __device__ __forceinline__ int pad_ld(int x) { return x | 1; }
 
-// Shared-memory carve-up of one PCG problem, in floats; every region starts
-// 16-byte aligned.  The same function sizes launches on the host and carves
-// on the device.
+// Shared-memory carve-up of one PCG problem, in elements of the working
+// precision; every region starts 16-byte aligned.  The first K block rows of
+// the operator and preconditioner blocks are staged (K = N+1: fully
+// resident; K = 0: everything read from L2/HBM each iteration).  The same
+// function sizes launches on the host and carves on the device.
 struct PcgLayout {
   int64_t p, r, w, x, v;            // vectors
-  int64_t m0, m1, iq, ir, pd, pe;   // matrices (resident schedule only)
+  int64_t iq, ir;                   // 1/q, 1/r (QP form)
+  int64_t m0, m1, pd, pe;           // staged blocks
   int64_t total;
 };
 
-__host__ __device__ inline PcgLayout pcg_layout(int op, bool resident, int N, int nx, int nu) {
+__host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, int nu) {
   PcgLayout L{};
   const int64_t n = N + 1, R4 = round_up(n * nx, 4);
+  const int64_t Ks = K < N ? K : N;  // staged off-diagonal slots
+  const int64_t ld = pad_ld(nx), ldb = pad_ld(nu > 0 ? nu : 1);
   int64_t o = 0;
   L.p = o; o += R4;
   L.r = o; o += R4;
@@ -36,23 +41,34 @@ __host__ __device__ inline PcgLayout pcg_layout(int op, bool resident, int N, in
   L.x = o; o += R4;
   L.v = o;
   if (op == kOpQp) o += round_up(n * nx + (int64_t)N * nu, 4);
-  L.m0 = L.m1 = L.iq = L.ir = L.pd = L.pe = o;
-  if (resident) {
-    const int64_t ld = pad_ld(nx), ldb = pad_ld(nu > 0 ? nu : 1);
-    if (op == kOpQp) {
-      L.m0 = o; o += round_up((int64_t)N * nx * ld, 4);    // A_k, row stride ld
-      L.m1 = o; o += round_up((int64_t)N * nx * ldb, 4);   // B_k, row stride ldb
-      L.iq = o; o += round_up(n * nx, 4);                  // 1 / q
-      L.ir = o; o += round_up((int64_t)N * nu, 4);         // 1 / r
-    } else {
-      L.m0 = o; o += round_up(n * nx * ld, 4);             // D_k
-      L.m1 = o; o += round_up((int64_t)N * nx * ld, 4);    // E_k
-    }
-    L.pd = o; o += round_up(n * nx * ld, 4);               // PD_k
-    L.pe = o; o += round_up((int64_t)N * nx * ld, 4);      // PE_k
+  L.iq = o;
+  if (op == kOpQp) o += round_up(n * nx, 4);
+  L.ir = o;
+  if (op == kOpQp) o += round_up((int64_t)N * nu, 4);
+  if (op == kOpQp) {
+    L.m0 = o; o += round_up(Ks * nx * ld, 4);    // A_k, row stride ld
+    L.m1 = o; o += round_up(Ks * nx * ldb, 4);   // B_k, row stride ldb
+  } else {
+    L.m0 = o; o += round_up((int64_t)K * nx * ld, 4);  // D_k
+    L.m1 = o; o += round_up(Ks * nx * ld, 4);          // E_k
   }
+  L.pd = o; o += round_up((int64_t)K * nx * ld, 4);    // PD_k
+  L.pe = o; o += round_up(Ks * nx * ld, 4);            // PE_k
   L.total = o;
   return L;
+}
+
+// Largest number of staged block rows whose layout fits in ``elems``; -1 when
+// not even the vectors fit.
+__host__ __device__ inline int pcg_max_resident(int op, int N, int nx, int nu, int64_t elems) {
+  if (pcg_layout(op, N + 1, N, nx, nu).total <= elems) return N + 1;
+  if (pcg_layout(op, 0, N, nx, nu).total > elems) return -1;
+  int lo = 0, hi = N;  // invariant: layout(lo) fits, layout(hi + 1) does not
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (pcg_layout(op, mid, N, nx, nu).total <= elems) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 // Arguments of a PCG launch (by value).
@@ -73,12 +89,15 @@ struct PcgArgs {
   float tol2;            // tol^2
   int32_t max_iter;      // <= 0: 10 (N+1) nx
   int32_t warm;          // 0, 1, 2 (see sspcg_options)
+  int64_t smem_elems;    // dynamic shared memory of the launch, in elements of the working precision
+  int32_t max_resident;  // cap on staged block rows (a schedule override); large = no cap
 };
 
 // PCG launch for one nx; dispatches to the instantiation for that nx.
-// f64: the FP64 path (QP operator form only).
-cudaError_t launch_pcg(int nx, int op, int red, bool resident, bool f64, const PcgArgs &a, int grid, int block,
-                       size_t smem, cudaStream_t st);
+// f64: the FP64 path (QP operator form only).  Each problem stages as many
+// block rows as fit in ``smem`` bytes (at most a.max_resident).
+cudaError_t launch_pcg(int nx, int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
+                       cudaStream_t st);
 int pcg_max_smem_bytes();
 
 // Schur build and preconditioner assembly; Real = float (FP32 blocks) or
@@ -87,11 +106,15 @@ template <typename Real>
 cudaError_t launch_schur_build(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots, const float *A,
                                const float *B, const float *qd, const float *rd, Real *D, Real *E,
                                cudaStream_t st, int sms);
+// Diagonal blocks of Phi^-1 (FP64 inverses), one thread per knot: every
+// knot of a launch must have the same nx.
 template <typename Real>
-cudaError_t launch_precond_build(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots,
-                                 const int64_t *off_start, int64_t total_off, int kind, const Real *D,
-                                 const Real *E, Real *PD, Real *PE, int32_t *status, cudaStream_t st, int sms,
-                                 int64_t off_elems);
+cudaError_t launch_precond_inv(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots, int nx, int kind,
+                               const Real *D, Real *PD, int32_t *status, cudaStream_t st);
+// Off-diagonal blocks of Phi^-1 (any mix of nx).
+template <typename Real>
+cudaError_t launch_precond_off(const ProbSet &ps, const int64_t *off_start, int64_t total_off, int kind,
+                               const Real *E, const Real *PD, Real *PE, cudaStream_t st, int sms, int64_t off_elems);
 cudaError_t launch_residual_qp(const ProbSet &ps, const float *A, const float *B, const float *qd, const float *rd,
                                const float *gamma, const float *lambda, double *relres_true, cudaStream_t st);
 

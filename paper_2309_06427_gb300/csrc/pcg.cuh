@@ -107,24 +107,38 @@ __device__ __forceinline__ Real bt_row(const MT *Md, const MT *Mo, int ld, int N
   return acc;
 }
 
-template <int NX, bool RES, typename Real, typename ST>
-__device__ __forceinline__ void stage_blocks(ST *dst, const ST *src, int nblk, int ld, int tid, int T) {
+template <int NX, typename Real>
+__device__ __forceinline__ void stage_blocks(Real *dst, const Real *src, int nblk, int ld, int tid, int T) {
   for (int e = tid; e < nblk * NX * NX; e += T) {
     const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
     dst[(b * NX + r) * ld + c] = src[e];
   }
 }
 
-template <int NX, int OP, int RED, bool RES, typename Real>
+// Operator and preconditioner blocks of one problem: the first K block rows
+// staged in shared memory (odd row strides), the rest read from global
+// memory (dense, row stride nx) through L1/L2.  Row k < K uses the staged
+// copies only (its off-diagonal slots k-1 and k are staged with it).
+template <typename Real>
+struct Views {
+  const Real *sA, *sB, *sD, *sE, *sPD, *sPE;      // staged (shared memory)
+  const float *gA, *gB, *gD, *gE;                 // FP32 inputs (global)
+  const Real *gPD, *gPE;                          // preconditioner (global)
+  int ld, ldb;                                    // staged row strides
+};
+
+template <int NX, int OP, int RED, typename Real>
 __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typename Red<RED, Real>::T *slots) {
   using R = Red<RED, Real>;
   using AccT = typename R::T;
-  // operator matrices: staged as Real in shared memory, or FP32 from global memory
-  using OpT = std::conditional_t<RES, Real, float>;
   const int p = d.id;  // output slot
   const int N = d.N, n = N + 1, nu = d.nu, R_ = n * NX;
   const int tid = threadIdx.x, T = blockDim.x;
-  const PcgLayout L = pcg_layout(OP, RES, N, NX, nu);
+  int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems);  // the host sized smem so that K >= 0
+  if (K > a.max_resident) K = a.max_resident;
+  if (K < 0) K = 0;
+  const int Ks = K < N ? K : N;
+  const PcgLayout L = pcg_layout(OP, K, N, NX, nu);
   Real *sp = sm + L.p, *sr = sm + L.r, *sw = sm + L.w, *sx = sm + L.x, *sv = sm + L.v;
   const float *gam = a.gamma + d.ovec;
   // lambda (global): read once for a warm start, written once at the end
@@ -136,64 +150,50 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     if (a.lambda_f32) reinterpret_cast<float *>(a.lambda)[d.ovec + row] = (float)v;
     else reinterpret_cast<Real *>(a.lambda)[d.ovec + row] = v;
   };
-  const Real *gPD = reinterpret_cast<const Real *>(a.PD) + d.odiag;
-  const Real *gPE = reinterpret_cast<const Real *>(a.PE) + d.ooff;
 
-  // ---- operator and preconditioner views ----
-  const OpT *mA = nullptr, *mB = nullptr, *mD = nullptr, *mE = nullptr;
-  const Real *mIq = nullptr, *mIr = nullptr, *mPD, *mPE;
-  const float *gq = a.qd + d.oq, *gr = a.rd + d.orr;
-  int lda, ldb;
-  if constexpr (RES) {
-    lda = pad_ld(NX);
-    ldb = pad_ld(nu > 0 ? nu : 1);
-    Real *s0 = sm + L.m0, *s1 = sm + L.m1, *spd = sm + L.pd, *spe = sm + L.pe;
-    stage_blocks<NX, RES, Real>(spd, gPD, n, lda, tid, T);
-    stage_blocks<NX, RES, Real>(spe, gPE, N, lda, tid, T);
-    if constexpr (OP == kOpQp) {
-      const float *gA = a.A + d.oA, *gB = a.B + d.oB;
-      Real *siq = sm + L.iq, *sir = sm + L.ir;
-      for (int e = tid; e < N * NX * NX; e += T) {
-        const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
-        s0[(b * NX + r) * lda + c] = (Real)gA[e];
-      }
-      for (int e = tid; e < N * NX * nu; e += T) {
-        const int row = e / nu, c = e - row * nu;
-        s1[row * ldb + c] = (Real)gB[e];
-      }
-      for (int e = tid; e < n * NX; e += T) siq[e] = Real(1) / (Real)gq[e];
-      for (int e = tid; e < N * nu; e += T) sir[e] = Real(1) / (Real)gr[e];
-      mA = s0; mB = s1; mIq = siq; mIr = sir;
-    } else {
-      const float *gD = a.D + d.odiag, *gE = a.E + d.ooff;
-      for (int e = tid; e < n * NX * NX; e += T) {
-        const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
-        s0[(b * NX + r) * lda + c] = (Real)gD[e];
-      }
-      for (int e = tid; e < N * NX * NX; e += T) {
-        const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
-        s1[(b * NX + r) * lda + c] = (Real)gE[e];
-      }
-      mD = s0; mE = s1;
-    }
-    mPD = spd; mPE = spe;
-  } else {
-    lda = NX;
-    ldb = nu;
-    if constexpr (OP == kOpQp) { mA = a.A + d.oA; mB = a.B + d.oB; }
-    else { mD = a.D + d.odiag; mE = a.E + d.ooff; }
-    mPD = gPD; mPE = gPE;
+  // ---- views and staging ----
+  Views<Real> V{};
+  V.ld = pad_ld(NX);
+  V.ldb = pad_ld(nu > 0 ? nu : 1);
+  V.gPD = reinterpret_cast<const Real *>(a.PD) + d.odiag;
+  V.gPE = reinterpret_cast<const Real *>(a.PE) + d.ooff;
+  {
+    Real *spd = sm + L.pd, *spe = sm + L.pe;
+    stage_blocks<NX>(spd, V.gPD, K, V.ld, tid, T);
+    stage_blocks<NX>(spe, V.gPE, Ks, V.ld, tid, T);
+    V.sPD = spd; V.sPE = spe;
   }
-
-  // 1/q_k[j] and 1/r_k[j]: staged reciprocals, or the same reciprocal formed on the fly.
-  auto inv_q = [&](int e) -> Real {
-    if constexpr (RES) return mIq[e];
-    else return Real(1) / (Real)__ldg(gq + e);
-  };
-  auto inv_r = [&](int e) -> Real {
-    if constexpr (RES) return mIr[e];
-    else return Real(1) / (Real)__ldg(gr + e);
-  };
+  const float *gq = a.qd + d.oq, *gr = a.rd + d.orr;
+  Real *siq = sm + L.iq, *sir = sm + L.ir;
+  if constexpr (OP == kOpQp) {
+    V.gA = a.A + d.oA;
+    V.gB = a.B + d.oB;
+    Real *s0 = sm + L.m0, *s1 = sm + L.m1;
+    for (int e = tid; e < Ks * NX * NX; e += T) {
+      const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
+      s0[(b * NX + r) * V.ld + c] = (Real)V.gA[e];
+    }
+    for (int e = tid; e < Ks * NX * nu; e += T) {
+      const int row = e / nu, c = e - row * nu;
+      s1[row * V.ldb + c] = (Real)V.gB[e];
+    }
+    for (int e = tid; e < n * NX; e += T) siq[e] = Real(1) / (Real)gq[e];
+    for (int e = tid; e < N * nu; e += T) sir[e] = Real(1) / (Real)gr[e];
+    V.sA = s0; V.sB = s1;
+  } else {
+    V.gD = a.D + d.odiag;
+    V.gE = a.E + d.ooff;
+    Real *s0 = sm + L.m0, *s1 = sm + L.m1;
+    for (int e = tid; e < K * NX * NX; e += T) {
+      const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
+      s0[(b * NX + r) * V.ld + c] = (Real)V.gD[e];
+    }
+    for (int e = tid; e < Ks * NX * NX; e += T) {
+      const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
+      s1[(b * NX + r) * V.ld + c] = (Real)V.gE[e];
+    }
+    V.sD = s0; V.sE = s1;
+  }
 
   // QP form, phase 1: sv = G^-1 C^T src (all threads), then a barrier.
   auto apply_S_phase1 = [&](const Real *src) {
@@ -205,22 +205,34 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
           const int k = it / NX, j = it - k * NX;
           Real acc = -src[it];
           if (k < N) {
-            const OpT *Ak = mA + (int64_t)k * NX * lda + j;  // column j of A_k
             const Real *pk1 = src + (k + 1) * NX;
+            if (k < K) {
+              const Real *Ak = V.sA + k * NX * V.ld + j;  // column j of A_k (staged)
 #pragma unroll
-            for (int l = 0; l < NX; ++l) acc = rfma((Real)ldm<RES>(Ak + l * lda), pk1[l], acc);
+              for (int l = 0; l < NX; ++l) acc = rfma(Ak[l * V.ld], pk1[l], acc);
+            } else {
+              const float *Ak = V.gA + (int64_t)k * NX * NX + j;
+#pragma unroll
+              for (int l = 0; l < NX; ++l) acc = rfma((Real)__ldg(Ak + l * NX), pk1[l], acc);
+            }
           }
-          sv[it] = acc * inv_q(it);
+          sv[it] = acc * siq[it];
         } else {
           const int t2 = it - nvx;
           const int k = (int)(((float)t2 + 0.5f) * inv_nu);
           const int j = t2 - k * nu;
-          const OpT *Bk = mB + (int64_t)k * NX * ldb + j;  // column j of B_k
           const Real *pk1 = src + (k + 1) * NX;
           Real acc = Real(0);
+          if (k < K) {
+            const Real *Bk = V.sB + k * NX * V.ldb + j;  // column j of B_k (staged)
 #pragma unroll
-          for (int l = 0; l < NX; ++l) acc = rfma((Real)ldm<RES>(Bk + l * ldb), pk1[l], acc);
-          sv[it] = acc * inv_r(t2);
+            for (int l = 0; l < NX; ++l) acc = rfma(Bk[l * V.ldb], pk1[l], acc);
+          } else {
+            const float *Bk = V.gB + (int64_t)k * NX * nu + j;
+#pragma unroll
+            for (int l = 0; l < NX; ++l) acc = rfma((Real)__ldg(Bk + l * nu), pk1[l], acc);
+          }
+          sv[it] = acc * sir[t2];
         }
       }
       __syncthreads();
@@ -231,24 +243,34 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     if constexpr (OP == kOpQp) {
       Real acc = -sv[k * NX + i];
       if (k > 0) {
-        const OpT *Ar = mA + (int64_t)(k - 1) * NX * lda + i * lda;  // row i of A_{k-1}
         const Real *vx = sv + (k - 1) * NX;
-#pragma unroll
-        for (int j = 0; j < NX; ++j) acc = rfma((Real)ldm<RES>(Ar + j), vx[j], acc);
-        const OpT *Br = mB + (int64_t)(k - 1) * NX * ldb + i * ldb;  // row i of B_{k-1}
         const Real *vu = sv + n * NX + (k - 1) * nu;
-        for (int j = 0; j < nu; ++j) acc = rfma((Real)ldm<RES>(Br + j), vu[j], acc);
+        if (k < K) {
+          const Real *Ar = V.sA + ((k - 1) * NX + i) * V.ld;  // row i of A_{k-1}
+#pragma unroll
+          for (int j = 0; j < NX; ++j) acc = rfma(Ar[j], vx[j], acc);
+          const Real *Br = V.sB + ((k - 1) * NX + i) * V.ldb;
+          for (int j = 0; j < nu; ++j) acc = rfma(Br[j], vu[j], acc);
+        } else {
+          const float *Ar = V.gA + ((int64_t)(k - 1) * NX + i) * NX;
+#pragma unroll
+          for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(Ar + j), vx[j], acc);
+          const float *Br = V.gB + ((int64_t)(k - 1) * NX + i) * nu;
+          for (int j = 0; j < nu; ++j) acc = rfma((Real)__ldg(Br + j), vu[j], acc);
+        }
       }
       return acc;
     } else {
-      return bt_row<NX, RES, Real>(mD, mE, lda, N, k, i, src);
+      return k < K ? bt_row<NX, true, Real>(V.sD, V.sE, V.ld, N, k, i, src)
+                   : bt_row<NX, false, Real>(V.gD, V.gE, NX, N, k, i, src);
     }
   };
   auto apply_P_row = [&](const Real *src, int k, int i) -> Real {
-    return bt_row<NX, RES, Real>(mPD, mPE, lda, N, k, i, src);
+    return k < K ? bt_row<NX, true, Real>(V.sPD, V.sPE, V.ld, N, k, i, src)
+                 : bt_row<NX, false, Real>(V.gPD, V.gPE, NX, N, k, i, src);
   };
 
-  if (RES) __syncthreads();  // staged matrices visible
+  __syncthreads();  // staged blocks and reciprocals visible
 
   // ---- r0 = gamma - S x0, z0 = Phi^-1 r0, p0 = z0 ----
   AccT g1[1] = {R::zero()};
@@ -363,7 +385,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
 
 // Persistent kernel: CTAs take problems from the work list, through an
 // atomic counter when one is given (largest problems first), else by stride.
-template <int NX, int OP, int RED, bool RES, typename Real>
+template <int NX, int OP, int RED, typename Real>
 __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
   extern __shared__ float4 smem4[];
   Real *sm = reinterpret_cast<Real *>(smem4);
@@ -384,37 +406,36 @@ __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
     if (w >= a.nwork) break;
     const ProbDesc d = a.ps.get(a.work ? a.work[w] : w);
     if (a.status[d.id] != kOk) continue;  // preconditioner failed for this problem
-    pcg_solve<NX, OP, RED, RES, Real>(a, d, sm, slots);
+    pcg_solve<NX, OP, RED, Real>(a, d, sm, slots);
   }
 }
 
-template <int NX, int OP, int RED, bool RES, typename Real>
+template <int NX, int OP, int RED, typename Real>
 cudaError_t launch_variant(const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
-  auto k = pcg_kernel<NX, OP, RED, RES, Real>;
+  auto k = pcg_kernel<NX, OP, RED, Real>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_max_smem_bytes());
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k<<<grid, block, smem, st>>>(a);
+  PcgArgs b = a;
+  b.smem_elems = (int64_t)(smem / sizeof(Real));
+  k<<<grid, block, smem, st>>>(b);
   return cudaGetLastError();
 }
 
 // All variants of one nx: FP32 with three reduction modes for both operator
-// forms and both schedules, and the FP64 path (QP form, FP64 reductions).
+// forms, and the FP64 path (QP form, FP64 reductions).
 template <int NX>
-cudaError_t launch_pcg_for_nx(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block,
-                              size_t smem, cudaStream_t st) {
+cudaError_t launch_pcg_for_nx(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
+                              cudaStream_t st) {
   if (f64) {
     if (op != kOpQp) return cudaErrorInvalidValue;
-    return res ? launch_variant<NX, kOpQp, kRedF64, true, double>(a, grid, block, smem, st)
-               : launch_variant<NX, kOpQp, kRedF64, false, double>(a, grid, block, smem, st);
+    return launch_variant<NX, kOpQp, kRedF64, double>(a, grid, block, smem, st);
   }
-#define SSPCG_PCG_CASE(OPV, REDV)                                                   \
-  if (op == OPV && red == REDV)                                                     \
-    return res ? launch_variant<NX, OPV, REDV, true, float>(a, grid, block, smem, st) \
-               : launch_variant<NX, OPV, REDV, false, float>(a, grid, block, smem, st);
+#define SSPCG_PCG_CASE(OPV, REDV) \
+  if (op == OPV && red == REDV) return launch_variant<NX, OPV, REDV, float>(a, grid, block, smem, st);
   SSPCG_PCG_CASE(kOpQp, kRedDf)
   SSPCG_PCG_CASE(kOpQp, kRedF32)
   SSPCG_PCG_CASE(kOpQp, kRedF64)
@@ -429,8 +450,8 @@ cudaError_t launch_pcg_for_nx(int op, int red, bool res, bool f64, const PcgArgs
 
 #define SSPCG_INSTANTIATE_PCG(NXV)                                                                           \
   namespace sspcg {                                                                                          \
-  cudaError_t launch_pcg_nx##NXV(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, \
-                                 size_t smem, cudaStream_t st) {                                             \
-    return launch_pcg_for_nx<NXV>(op, red, res, f64, a, grid, block, smem, st);                               \
+  cudaError_t launch_pcg_nx##NXV(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, \
+                                 cudaStream_t st) {                                                          \
+    return launch_pcg_for_nx<NXV>(op, red, f64, a, grid, block, smem, st);                                    \
   }                                                                                                          \
   }

@@ -3,66 +3,66 @@
 
 namespace sspcg {
 
-cudaError_t launch_pcg_nx1(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx2(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx3(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx4(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx5(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx6(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx7(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx8(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx9(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx10(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx11(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx12(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx13(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx14(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx15(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx16(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx17(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx18(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx19(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx20(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx21(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx22(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx23(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx24(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx25(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx26(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx27(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_pcg_nx28(int op, int red, bool res, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx1(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx2(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx3(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx4(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx5(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx6(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx7(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx8(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx9(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx10(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx11(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx12(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx13(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx14(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx15(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx16(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx17(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx18(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx19(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx20(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx21(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx22(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx23(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx24(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx25(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx26(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx27(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_pcg_nx28(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st);
 
-cudaError_t launch_pcg(int nx, int op, int red, bool resident, bool f64, const PcgArgs &a, int grid, int block,
-                       size_t smem, cudaStream_t st) {
+cudaError_t launch_pcg(int nx, int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
+                       cudaStream_t st) {
   switch (nx) {
-    case 1: return launch_pcg_nx1(op, red, resident, f64, a, grid, block, smem, st);
-    case 2: return launch_pcg_nx2(op, red, resident, f64, a, grid, block, smem, st);
-    case 3: return launch_pcg_nx3(op, red, resident, f64, a, grid, block, smem, st);
-    case 4: return launch_pcg_nx4(op, red, resident, f64, a, grid, block, smem, st);
-    case 5: return launch_pcg_nx5(op, red, resident, f64, a, grid, block, smem, st);
-    case 6: return launch_pcg_nx6(op, red, resident, f64, a, grid, block, smem, st);
-    case 7: return launch_pcg_nx7(op, red, resident, f64, a, grid, block, smem, st);
-    case 8: return launch_pcg_nx8(op, red, resident, f64, a, grid, block, smem, st);
-    case 9: return launch_pcg_nx9(op, red, resident, f64, a, grid, block, smem, st);
-    case 10: return launch_pcg_nx10(op, red, resident, f64, a, grid, block, smem, st);
-    case 11: return launch_pcg_nx11(op, red, resident, f64, a, grid, block, smem, st);
-    case 12: return launch_pcg_nx12(op, red, resident, f64, a, grid, block, smem, st);
-    case 13: return launch_pcg_nx13(op, red, resident, f64, a, grid, block, smem, st);
-    case 14: return launch_pcg_nx14(op, red, resident, f64, a, grid, block, smem, st);
-    case 15: return launch_pcg_nx15(op, red, resident, f64, a, grid, block, smem, st);
-    case 16: return launch_pcg_nx16(op, red, resident, f64, a, grid, block, smem, st);
-    case 17: return launch_pcg_nx17(op, red, resident, f64, a, grid, block, smem, st);
-    case 18: return launch_pcg_nx18(op, red, resident, f64, a, grid, block, smem, st);
-    case 19: return launch_pcg_nx19(op, red, resident, f64, a, grid, block, smem, st);
-    case 20: return launch_pcg_nx20(op, red, resident, f64, a, grid, block, smem, st);
-    case 21: return launch_pcg_nx21(op, red, resident, f64, a, grid, block, smem, st);
-    case 22: return launch_pcg_nx22(op, red, resident, f64, a, grid, block, smem, st);
-    case 23: return launch_pcg_nx23(op, red, resident, f64, a, grid, block, smem, st);
-    case 24: return launch_pcg_nx24(op, red, resident, f64, a, grid, block, smem, st);
-    case 25: return launch_pcg_nx25(op, red, resident, f64, a, grid, block, smem, st);
-    case 26: return launch_pcg_nx26(op, red, resident, f64, a, grid, block, smem, st);
-    case 27: return launch_pcg_nx27(op, red, resident, f64, a, grid, block, smem, st);
-    case 28: return launch_pcg_nx28(op, red, resident, f64, a, grid, block, smem, st);
+    case 1: return launch_pcg_nx1(op, red, f64, a, grid, block, smem, st);
+    case 2: return launch_pcg_nx2(op, red, f64, a, grid, block, smem, st);
+    case 3: return launch_pcg_nx3(op, red, f64, a, grid, block, smem, st);
+    case 4: return launch_pcg_nx4(op, red, f64, a, grid, block, smem, st);
+    case 5: return launch_pcg_nx5(op, red, f64, a, grid, block, smem, st);
+    case 6: return launch_pcg_nx6(op, red, f64, a, grid, block, smem, st);
+    case 7: return launch_pcg_nx7(op, red, f64, a, grid, block, smem, st);
+    case 8: return launch_pcg_nx8(op, red, f64, a, grid, block, smem, st);
+    case 9: return launch_pcg_nx9(op, red, f64, a, grid, block, smem, st);
+    case 10: return launch_pcg_nx10(op, red, f64, a, grid, block, smem, st);
+    case 11: return launch_pcg_nx11(op, red, f64, a, grid, block, smem, st);
+    case 12: return launch_pcg_nx12(op, red, f64, a, grid, block, smem, st);
+    case 13: return launch_pcg_nx13(op, red, f64, a, grid, block, smem, st);
+    case 14: return launch_pcg_nx14(op, red, f64, a, grid, block, smem, st);
+    case 15: return launch_pcg_nx15(op, red, f64, a, grid, block, smem, st);
+    case 16: return launch_pcg_nx16(op, red, f64, a, grid, block, smem, st);
+    case 17: return launch_pcg_nx17(op, red, f64, a, grid, block, smem, st);
+    case 18: return launch_pcg_nx18(op, red, f64, a, grid, block, smem, st);
+    case 19: return launch_pcg_nx19(op, red, f64, a, grid, block, smem, st);
+    case 20: return launch_pcg_nx20(op, red, f64, a, grid, block, smem, st);
+    case 21: return launch_pcg_nx21(op, red, f64, a, grid, block, smem, st);
+    case 22: return launch_pcg_nx22(op, red, f64, a, grid, block, smem, st);
+    case 23: return launch_pcg_nx23(op, red, f64, a, grid, block, smem, st);
+    case 24: return launch_pcg_nx24(op, red, f64, a, grid, block, smem, st);
+    case 25: return launch_pcg_nx25(op, red, f64, a, grid, block, smem, st);
+    case 26: return launch_pcg_nx26(op, red, f64, a, grid, block, smem, st);
+    case 27: return launch_pcg_nx27(op, red, f64, a, grid, block, smem, st);
+    case 28: return launch_pcg_nx28(op, red, f64, a, grid, block, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }
