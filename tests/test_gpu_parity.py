@@ -221,7 +221,7 @@ def test_inputless_dynamics_nu0():
     for kind in ("sym", "add", "bj"):
         _, _, x, it_o, _, _, st_o = block.solve_problem(p, kind, 1e-6)
         lam, it, rr, st = gpu_solve_qp_f64(p, kind, 1e-6)
-        assert st == 0 and abs(it - it_o) <= ITER_TOL and rel(lam, x) <= 1e-7
+        assert st == 0 and iters_ok(it, it_o, unknowns=p.n * p.nx) and rel(lam, x) <= 1e-7
         lam, it, rr, st = gpu_solve_qp(p, kind, 1e-6)
         assert st == 0 and rr <= 1e-6 and it_o - 1 <= it <= 1.5 * it_o
         assert rel(lam, x) <= LAMBDA_RTOL
