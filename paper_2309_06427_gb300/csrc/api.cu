@@ -147,7 +147,7 @@ struct NxGroup {
   int32_t nprob = 0;
   int64_t knots = 0;
   ProbDesc *d_desc = nullptr;
-  int64_t *d_knot_start = nullptr;
+  int2 *d_refs = nullptr;  // (index into d_desc, block row) per knot
 };
 
 struct sspcg_plan {
@@ -158,13 +158,13 @@ struct sspcg_plan {
   std::vector<int64_t> offsets[SSPCG_NUM_ARRAYS];
   int64_t sizes[SSPCG_NUM_ARRAYS] = {};
   ProbDesc *d_desc = nullptr;
-  int64_t *d_knot_start = nullptr, *d_off_start = nullptr;
+  int2 *d_kref = nullptr, *d_oref = nullptr;  // (problem, block row) per knot / off-diagonal block
   int64_t total_knots = 0, total_off = 0;
   // FP64 subset: descriptors whose odiag/ooff point into plan-owned FP64 blocks
   int32_t ntiny = 0;
   std::vector<ProbDesc> tdesc;
   ProbDesc *d_tdesc = nullptr;
-  int64_t *d_tknot_start = nullptr, *d_toff_start = nullptr;
+  int2 *d_tkref = nullptr, *d_toref = nullptr;
   int64_t tknots = 0, toff = 0, t_diag = 0, t_offe = 0;
   double *D64 = nullptr, *E64 = nullptr, *PD64 = nullptr, *PE64 = nullptr;
   // PCG launch groups
@@ -192,15 +192,15 @@ namespace {
 void plan_free(sspcg_plan *p) {
   if (!p) return;
   if (p->graph) cudaGraphExecDestroy(p->graph);
-  for (void *ptr : {(void *)p->d_desc, (void *)p->d_knot_start, (void *)p->d_off_start, (void *)p->d_tdesc,
-                    (void *)p->d_tknot_start, (void *)p->d_toff_start, (void *)p->D64, (void *)p->E64,
+  for (void *ptr : {(void *)p->d_desc, (void *)p->d_kref, (void *)p->d_oref, (void *)p->d_tdesc,
+                    (void *)p->d_tkref, (void *)p->d_toref, (void *)p->D64, (void *)p->E64,
                     (void *)p->PD64, (void *)p->PE64, (void *)p->d_work, (void *)p->d_counters, (void *)p->hbuf,
                     (void *)p->hint, (void *)p->hdbl})
     cudaFree(ptr);
   for (auto *v : {&p->nxg_all, &p->nxg_tiny})
     for (NxGroup &g : *v) {
       cudaFree(g.d_desc);
-      cudaFree(g.d_knot_start);
+      cudaFree(g.d_refs);
     }
   for (auto s : p->side) cudaStreamDestroy(s);
   for (auto e : p->ev) cudaEventDestroy(e);
@@ -311,25 +311,31 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
   return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
 }
 
-// Split ``members`` of ``descs`` by nx into device descriptor subsets with knot prefixes.
+// (problem, block row) table of the knots (first = 0) or off-diagonal blocks
+// (first = 1) of ``descs``.
+std::vector<int2> row_refs(const std::vector<ProbDesc> &descs, int first) {
+  std::vector<int2> r;
+  for (size_t i = 0; i < descs.size(); ++i)
+    for (int k = first; k <= descs[i].N; ++k) r.push_back(make_int2((int)i, k));
+  return r;
+}
+
+// Split ``members`` of ``descs`` by nx into device descriptor subsets with knot tables.
 cudaError_t make_nx_groups(const std::vector<ProbDesc> &descs, const std::vector<int32_t> &members,
                            std::vector<NxGroup> &out) {
   for (int nx = 1; nx <= kMaxNx; ++nx) {
     std::vector<ProbDesc> sub;
-    std::vector<int64_t> ks(1, 0);
     for (int32_t i : members)
-      if (descs[i].nx == nx) {
-        sub.push_back(descs[i]);
-        ks.push_back(ks.back() + descs[i].N + 1);
-      }
+      if (descs[i].nx == nx) sub.push_back(descs[i]);
     if (sub.empty()) continue;
+    const std::vector<int2> refs = row_refs(sub, 0);
     NxGroup g;
     g.nx = nx;
     g.nprob = (int32_t)sub.size();
-    g.knots = ks.back();
+    g.knots = (int64_t)refs.size();
     out.push_back(g);  // pushed first so that plan_free releases partial uploads
     cudaError_t e = upload(&out.back().d_desc, sub);
-    if (e == cudaSuccess) e = upload(&out.back().d_knot_start, ks);
+    if (e == cudaSuccess) e = upload(&out.back().d_refs, refs);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -510,16 +516,16 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
   if (nprob > 0) {
     cudaError_t e;
     if ((e = upload(&p->d_desc, p->hdesc)) != cudaSuccess) return fail(cuda_fail(e));
-    if ((e = upload(&p->d_knot_start, knot_start)) != cudaSuccess) return fail(cuda_fail(e));
-    if ((e = upload(&p->d_off_start, off_start)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = upload(&p->d_kref, row_refs(p->hdesc, 0))) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = upload(&p->d_oref, row_refs(p->hdesc, 1))) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = make_nx_groups(p->hdesc, all, p->nxg_all)) != cudaSuccess) return fail(cuda_fail(e));
     if (p->ntiny > 0) {
       std::vector<int32_t> tl(p->ntiny);
       std::iota(tl.begin(), tl.end(), 0);
       if ((e = make_nx_groups(p->tdesc, tl, p->nxg_tiny)) != cudaSuccess) return fail(cuda_fail(e));
       if ((e = upload(&p->d_tdesc, p->tdesc)) != cudaSuccess) return fail(cuda_fail(e));
-      if ((e = upload(&p->d_tknot_start, tknot)) != cudaSuccess) return fail(cuda_fail(e));
-      if ((e = upload(&p->d_toff_start, toff)) != cudaSuccess) return fail(cuda_fail(e));
+      if ((e = upload(&p->d_tkref, row_refs(p->tdesc, 0))) != cudaSuccess) return fail(cuda_fail(e));
+      if ((e = upload(&p->d_toref, row_refs(p->tdesc, 1))) != cudaSuccess) return fail(cuda_fail(e));
       const int64_t td = std::max<int64_t>(p->t_diag, 2), to = std::max<int64_t>(p->t_offe, 2);
       if ((e = cudaMalloc(&p->D64, sizeof(double) * td)) != cudaSuccess) return fail(cuda_fail(e));
       if ((e = cudaMalloc(&p->PD64, sizeof(double) * td)) != cudaSuccess) return fail(cuda_fail(e));
@@ -618,7 +624,7 @@ sspcg_status sspcg_build_schur_batched(sspcg_plan *plan, const float *A, const f
   if (plan->nprob == 0) return SSPCG_OK;
   if (!qd || !D || !aligned16(qd) || !aligned16(D)) return SSPCG_ERR_INVALID_ARG;
   if (plan->total_off > 0 && (!A || !rd || !E || !B)) return SSPCG_ERR_INVALID_ARG;
-  SSPCG_CUDA(launch_schur_build<float>(plan_set(plan), plan->d_knot_start, plan->total_knots, A, B, qd, rd, D, E,
+  SSPCG_CUDA(launch_schur_build<float>(plan_set(plan), plan->d_kref, plan->total_knots, A, B, qd, rd, D, E,
                                        (cudaStream_t)stream, device_sms()));
   return SSPCG_OK;
 }
@@ -631,9 +637,9 @@ sspcg_status sspcg_build_precond_batched(sspcg_plan *plan, sspcg_precond kind, c
   cudaStream_t st = (cudaStream_t)stream;
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
   for (const NxGroup &g : plan->nxg_all)
-    SSPCG_CUDA(launch_precond_inv<float>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_knot_start, g.knots, g.nx,
+    SSPCG_CUDA(launch_precond_inv<float>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_refs, g.knots, g.nx,
                                          (int)kind, D, PD, status, st));
-  SSPCG_CUDA(launch_precond_off<float>(plan_set(plan), plan->d_off_start, plan->total_off, (int)kind, E, PD, PE, st,
+  SSPCG_CUDA(launch_precond_off<float>(plan_set(plan), plan->d_oref, plan->total_off, (int)kind, E, PD, PE, st,
                                        device_sms(), plan->sizes[SSPCG_ARRAY_OFF]));
   return SSPCG_OK;
 }
@@ -725,12 +731,12 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
   if ((s = sspcg_build_schur_batched(plan, A, B, qd, rd, D, E, stream)) != SSPCG_OK) return s;
   if ((s = sspcg_build_precond_batched(plan, kind, D, E, PD, PE, status, stream)) != SSPCG_OK) return s;
   if (plan->ntiny > 0) {
-    SSPCG_CUDA(launch_schur_build<double>(tiny_set(plan), plan->d_tknot_start, plan->tknots, A, B, qd, rd, plan->D64,
+    SSPCG_CUDA(launch_schur_build<double>(tiny_set(plan), plan->d_tkref, plan->tknots, A, B, qd, rd, plan->D64,
                                           plan->E64, st, device_sms()));
     for (const NxGroup &g : plan->nxg_tiny)
-      SSPCG_CUDA(launch_precond_inv<double>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_knot_start, g.knots, g.nx,
+      SSPCG_CUDA(launch_precond_inv<double>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_refs, g.knots, g.nx,
                                             (int)kind, plan->D64, plan->PD64, status, st));
-    SSPCG_CUDA(launch_precond_off<double>(tiny_set(plan), plan->d_toff_start, plan->toff, (int)kind, plan->E64,
+    SSPCG_CUDA(launch_precond_off<double>(tiny_set(plan), plan->d_toref, plan->toff, (int)kind, plan->E64,
                                           plan->PD64, plan->PE64, st, device_sms(), plan->t_offe));
   }
   plan->build_timed = true;

@@ -1,6 +1,6 @@
 // Schur-block build (Sec. II-A) and preconditioner assembly (Eq. stair_inv,
 // Sec. III, Sec. IV, Eq. jacobi).  One warp per knot; the batch is a flat
-// list of knots, each warp finding its problem by binary search.
+// list of knots whose (problem, block row) pairs the plan tabulates.
 #include <algorithm>
 
 #include "common.cuh"
@@ -20,7 +20,7 @@ constexpr int kBuildWarps = 4;  // warps per CTA of the build kernels
 // Shared memory per warp: AQ (nx*nx), A (nx*nx), BR (nx*nu), B (nx*nu), 1/q_k (nx).
 // ---------------------------------------------------------------------------
 template <typename Real>
-__global__ void __launch_bounds__(kBuildWarps * 32) schur_build_kernel(ProbSet ps, const int64_t *knot_start,
+__global__ void __launch_bounds__(kBuildWarps * 32) schur_build_kernel(ProbSet ps, const int2 *refs,
                                                                       int64_t total_knots, const float *__restrict__ A,
                                                                       const float *__restrict__ B,
                                                                       const float *__restrict__ qd,
@@ -35,9 +35,9 @@ __global__ void __launch_bounds__(kBuildWarps * 32) schur_build_kernel(ProbSet p
   Real *sB = sBR + kMaxNx * kMaxNx;
   Real *sIq = sB + kMaxNx * kMaxNx;
   for (int64_t g = (int64_t)blockIdx.x * kBuildWarps + wid; g < total_knots; g += (int64_t)gridDim.x * kBuildWarps) {
-    const int p = knot_start ? find_problem(knot_start, ps.nprob, g) : 0;
-    const ProbDesc d = ps.get(p);
-    const int k = (int)(g - (knot_start ? knot_start[p] : 0));
+    const int2 ref = refs ? refs[g] : make_int2(0, (int)g);  // (problem, block row)
+    const ProbDesc d = ps.get(ref.x);
+    const int k = ref.y;
     const int nx = d.nx, nu = d.nu, nn = nx * nx;
     Real *Dk = D + d.odiag + (int64_t)k * nn;
     if (k == 0) {
@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) schur_build_kernel(ProbSet p
     const float *qk = qd + d.oq + (int64_t)k * nx;
     const float *rp = rd + d.orr + (int64_t)(k - 1) * nu;
     Real *Ek = E + d.ooff + (int64_t)(k - 1) * nn;
+#pragma unroll 4
     for (int e = lane; e < nn; e += 32) {
       const int l = e % nx;
       const Real a = (Real)Ak[e];
@@ -105,18 +106,22 @@ __device__ __forceinline__ double rcp_f64(double x) {
   return y;
 }
 
-__host__ __device__ __forceinline__ int inv_stride(int nx) { return (nx * nx) | 1; }
+// Per-thread storage: the packed lower triangle, row i at offset i(i+1)/2;
+// the per-thread stride is odd (8-byte words) so that a warp's accesses to
+// the same entry fall in distinct banks.
+__host__ __device__ __forceinline__ int inv_stride(int nx) { return (nx * (nx + 1) / 2) | 1; }
+__device__ __forceinline__ int tri(int i, int c) { return i * (i + 1) / 2 + c; }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int64_t *knot_start, int64_t total_knots,
+__global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int2 *refs, int64_t total_knots,
                                                          int nx, int kind, const Real *__restrict__ D, Real *PD,
                                                          int32_t *status) {
   extern __shared__ double dsm[];
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total_knots) return;
-  const int p = knot_start ? find_problem(knot_start, ps.nprob, g) : 0;
-  const ProbDesc d = ps.get(p);
-  const int k = (int)(g - (knot_start ? knot_start[p] : 0));
+  const int2 ref = refs ? refs[g] : make_int2(0, (int)g);  // (problem, block row)
+  const ProbDesc d = ps.get(ref.x);
+  const int k = ref.y;
   const int nn = nx * nx;
   const Real *Dk = D + d.odiag + (int64_t)k * nn;
   Real *PDk = PD + d.odiag + (int64_t)k * nn;
@@ -133,10 +138,10 @@ __global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int6
   }
   double *M = dsm + (int64_t)threadIdx.x * inv_stride(nx);
   for (int i = 0; i < nx; ++i)
-    for (int c = 0; c <= i; ++c) M[i * nx + c] = (double)Dk[i * nx + c];
+    for (int c = 0; c <= i; ++c) M[tri(i, c)] = (double)Dk[i * nx + c];
   // LDL^T: after step j, M(j,j) = 1/d_j and M(i,j) = L(i,j) for i > j.
   for (int j = 0; j < nx; ++j) {
-    const double djj = M[j * nx + j];
+    const double djj = M[tri(j, j)];
     if (!(djj > 0.0) || !isfinite(djj)) {
       status[d.id] = kNotSpd;
       for (int e = 0; e < nn; ++e) PDk[e] = Real(0);
@@ -144,25 +149,30 @@ __global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int6
     }
     const double inv = rcp_f64(djj);
     for (int i = nx - 1; i > j; --i) {
-      const double lij = M[i * nx + j] * inv;
-      for (int c = j + 1; c <= i; ++c) M[i * nx + c] = fma(-lij, M[c * nx + j], M[i * nx + c]);
-      M[i * nx + j] = lij;
+      double *Mi = M + tri(i, 0);
+      const double lij = Mi[j] * inv;
+      for (int c = j + 1; c <= i; ++c) Mi[c] = fma(-lij, M[tri(c, j)], Mi[c]);
+      Mi[j] = lij;
     }
-    M[j * nx + j] = inv;
+    M[tri(j, j)] = inv;
   }
   // W = L^-1 (unit lower) in place, column by column.
   for (int j = 0; j + 1 < nx; ++j) {
     for (int i = j + 1; i < nx; ++i) {
-      double s = M[i * nx + j];
-      for (int t = j + 1; t < i; ++t) s = fma(M[i * nx + t], M[t * nx + j], s);
-      M[i * nx + j] = -s;
+      const double *Mi = M + tri(i, 0);
+      double s = Mi[j];
+      for (int t = j + 1; t < i; ++t) s = fma(Mi[t], M[tri(t, j)], s);
+      M[tri(i, j)] = -s;
     }
   }
   // D^-1 = W^T diag(1/d) W, lower triangle, mirrored.
   for (int i = 0; i < nx; ++i) {
     for (int j = 0; j <= i; ++j) {
-      double s = M[i * nx + i] * (i == j ? 1.0 : M[i * nx + j]);
-      for (int t = i + 1; t < nx; ++t) s = fma(M[t * nx + i] * M[t * nx + t], M[t * nx + j], s);
+      double s = M[tri(i, i)] * (i == j ? 1.0 : M[tri(i, j)]);
+      for (int t = i + 1; t < nx; ++t) {
+        const double *Mt = M + tri(t, 0);
+        s = fma(Mt[i] * Mt[t], Mt[j], s);
+      }
       const Real f = (Real)s;
       PDk[i * nx + j] = f;
       PDk[j * nx + i] = f;
@@ -176,7 +186,7 @@ __global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int6
 // Shared memory per warp: PD_k, E, PD_{k-1}, T = PD_k E (4 * nx * nx floats).
 // ---------------------------------------------------------------------------
 template <typename Real>
-__global__ void __launch_bounds__(kBuildWarps * 32) precond_off_kernel(ProbSet ps, const int64_t *off_start,
+__global__ void __launch_bounds__(kBuildWarps * 32) precond_off_kernel(ProbSet ps, const int2 *refs,
                                                                       int64_t total_off, Real c,
                                                                       const Real *__restrict__ E,
                                                                       const Real *__restrict__ PD, Real *PE) {
@@ -189,14 +199,15 @@ __global__ void __launch_bounds__(kBuildWarps * 32) precond_off_kernel(ProbSet p
   Real *sP0 = sE + kMaxNx * kMaxNx;
   Real *sT = sP0 + kMaxNx * kMaxNx;
   for (int64_t g = (int64_t)blockIdx.x * kBuildWarps + wid; g < total_off; g += (int64_t)gridDim.x * kBuildWarps) {
-    const int p = off_start ? find_problem(off_start, ps.nprob, g) : 0;
-    const ProbDesc d = ps.get(p);
-    const int k = 1 + (int)(g - (off_start ? off_start[p] : 0));  // block row k >= 1
+    const int2 ref = refs ? refs[g] : make_int2(0, (int)g + 1);  // (problem, block row k >= 1)
+    const ProbDesc d = ps.get(ref.x);
+    const int k = ref.y;
     const int nx = d.nx, nn = nx * nx;
     const Real *P1 = PD + d.odiag + (int64_t)k * nn;
     const Real *P0 = PD + d.odiag + (int64_t)(k - 1) * nn;
     const Real *Ek = E + d.ooff + (int64_t)(k - 1) * nn;
     Real *PEk = PE + d.ooff + (int64_t)(k - 1) * nn;
+#pragma unroll 4
     for (int e = lane; e < nn; e += 32) {
       sP1[e] = P1[e];
       sE[e] = Ek[e];
@@ -230,7 +241,7 @@ static int build_grid(int64_t items, int sms) {
 }
 
 template <typename Real>
-cudaError_t launch_schur_build(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots, const float *A,
+cudaError_t launch_schur_build(const ProbSet &ps, const int2 *refs, int64_t total_knots, const float *A,
                                const float *B, const float *qd, const float *rd, Real *D, Real *E,
                                cudaStream_t st, int sms) {
   if (total_knots == 0) return cudaSuccess;
@@ -242,13 +253,13 @@ cudaError_t launch_schur_build(const ProbSet &ps, const int64_t *knot_start, int
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  schur_build_kernel<Real><<<build_grid(total_knots, sms), kBuildWarps * 32, smem, st>>>(ps, knot_start, total_knots,
+  schur_build_kernel<Real><<<build_grid(total_knots, sms), kBuildWarps * 32, smem, st>>>(ps, refs, total_knots,
                                                                                           A, B, qd, rd, D, E);
   return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_precond_inv(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots, int nx, int kind,
+cudaError_t launch_precond_inv(const ProbSet &ps, const int2 *refs, int64_t total_knots, int nx, int kind,
                                const Real *D, Real *PD, int32_t *status, cudaStream_t st) {
   if (total_knots == 0) return cudaSuccess;
   static int attr_set = 0;
@@ -264,13 +275,13 @@ cudaError_t launch_precond_inv(const ProbSet &ps, const int64_t *knot_start, int
     attr_set = 1;
   }
   const int64_t grid = cdiv(total_knots, threads);
-  precond_inv_kernel<Real><<<(unsigned)grid, threads, smem, st>>>(ps, knot_start, total_knots, nx, kind, D, PD,
+  precond_inv_kernel<Real><<<(unsigned)grid, threads, smem, st>>>(ps, refs, total_knots, nx, kind, D, PD,
                                                                    status);
   return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_precond_off(const ProbSet &ps, const int64_t *off_start, int64_t total_off, int kind,
+cudaError_t launch_precond_off(const ProbSet &ps, const int2 *refs, int64_t total_off, int kind,
                                const Real *E, const Real *PD, Real *PE, cudaStream_t st, int sms, int64_t off_elems) {
   if (total_off == 0) return cudaSuccess;
   if (kind == 2 || kind == 3) {  // block-Jacobi, Jacobi: no off-diagonal blocks
@@ -285,23 +296,23 @@ cudaError_t launch_precond_off(const ProbSet &ps, const int64_t *off_start, int6
     attr = true;
   }
   const Real c = (kind == 0) ? Real(1) : Real(0.5);
-  precond_off_kernel<Real><<<build_grid(total_off, sms), kBuildWarps * 32, smem_o, st>>>(ps, off_start, total_off, c,
+  precond_off_kernel<Real><<<build_grid(total_off, sms), kBuildWarps * 32, smem_o, st>>>(ps, refs, total_off, c,
                                                                                           E, PD, PE);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_schur_build<float>(const ProbSet &, const int64_t *, int64_t, const float *, const float *,
+template cudaError_t launch_schur_build<float>(const ProbSet &, const int2 *, int64_t, const float *, const float *,
                                                const float *, const float *, float *, float *, cudaStream_t, int);
-template cudaError_t launch_schur_build<double>(const ProbSet &, const int64_t *, int64_t, const float *,
+template cudaError_t launch_schur_build<double>(const ProbSet &, const int2 *, int64_t, const float *,
                                                 const float *, const float *, const float *, double *, double *,
                                                 cudaStream_t, int);
-template cudaError_t launch_precond_inv<float>(const ProbSet &, const int64_t *, int64_t, int, int, const float *,
+template cudaError_t launch_precond_inv<float>(const ProbSet &, const int2 *, int64_t, int, int, const float *,
                                                float *, int32_t *, cudaStream_t);
-template cudaError_t launch_precond_inv<double>(const ProbSet &, const int64_t *, int64_t, int, int, const double *,
+template cudaError_t launch_precond_inv<double>(const ProbSet &, const int2 *, int64_t, int, int, const double *,
                                                 double *, int32_t *, cudaStream_t);
-template cudaError_t launch_precond_off<float>(const ProbSet &, const int64_t *, int64_t, int, const float *,
+template cudaError_t launch_precond_off<float>(const ProbSet &, const int2 *, int64_t, int, const float *,
                                                const float *, float *, cudaStream_t, int, int64_t);
-template cudaError_t launch_precond_off<double>(const ProbSet &, const int64_t *, int64_t, int, const double *,
+template cudaError_t launch_precond_off<double>(const ProbSet &, const int2 *, int64_t, int, const double *,
                                                 const double *, double *, cudaStream_t, int, int64_t);
 
 }  // namespace sspcg

@@ -101,19 +101,20 @@ cudaError_t launch_pcg(int nx, int op, int red, bool f64, const PcgArgs &a, int 
 int pcg_max_smem_bytes();
 
 // Schur build and preconditioner assembly; Real = float (FP32 blocks) or
-// double (the FP64 path).
+// double (the FP64 path).  refs[i] = (problem, block row) of work item i
+// (nullptr: one problem, item i is block row i, or i + 1 for off-diagonals).
 template <typename Real>
-cudaError_t launch_schur_build(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots, const float *A,
+cudaError_t launch_schur_build(const ProbSet &ps, const int2 *refs, int64_t total_knots, const float *A,
                                const float *B, const float *qd, const float *rd, Real *D, Real *E,
                                cudaStream_t st, int sms);
 // Diagonal blocks of Phi^-1 (FP64 inverses), one thread per knot: every
 // knot of a launch must have the same nx.
 template <typename Real>
-cudaError_t launch_precond_inv(const ProbSet &ps, const int64_t *knot_start, int64_t total_knots, int nx, int kind,
+cudaError_t launch_precond_inv(const ProbSet &ps, const int2 *refs, int64_t total_knots, int nx, int kind,
                                const Real *D, Real *PD, int32_t *status, cudaStream_t st);
 // Off-diagonal blocks of Phi^-1 (any mix of nx).
 template <typename Real>
-cudaError_t launch_precond_off(const ProbSet &ps, const int64_t *off_start, int64_t total_off, int kind,
+cudaError_t launch_precond_off(const ProbSet &ps, const int2 *refs, int64_t total_off, int kind,
                                const Real *E, const Real *PD, Real *PE, cudaStream_t st, int sms, int64_t off_elems);
 cudaError_t launch_residual_qp(const ProbSet &ps, const float *A, const float *B, const float *qd, const float *rd,
                                const float *gamma, const float *lambda, double *relres_true, cudaStream_t st);
