@@ -167,6 +167,10 @@ struct sspcg_plan {
   int2 *d_tkref = nullptr, *d_toref = nullptr;
   int64_t tknots = 0, toff = 0, t_diag = 0, t_offe = 0;
   double *D64 = nullptr, *E64 = nullptr, *PD64 = nullptr, *PE64 = nullptr;
+  // transposed A, B, PE of the problems that do not fit in shared memory
+  int2 *d_sref = nullptr;  // (problem, block row >= 1) of their off-diagonal slots
+  int64_t sslots = 0;
+  float *At = nullptr, *Bt = nullptr, *PEt = nullptr;
   // PCG launch groups
   int32_t *d_work = nullptr;
   int32_t *d_counters = nullptr;
@@ -194,7 +198,8 @@ void plan_free(sspcg_plan *p) {
   if (p->graph) cudaGraphExecDestroy(p->graph);
   for (void *ptr : {(void *)p->d_desc, (void *)p->d_kref, (void *)p->d_oref, (void *)p->d_tdesc,
                     (void *)p->d_tkref, (void *)p->d_toref, (void *)p->D64, (void *)p->E64,
-                    (void *)p->PD64, (void *)p->PE64, (void *)p->d_work, (void *)p->d_counters, (void *)p->hbuf,
+                    (void *)p->PD64, (void *)p->PE64, (void *)p->d_sref, (void *)p->At, (void *)p->Bt,
+                    (void *)p->PEt, (void *)p->d_work, (void *)p->d_counters, (void *)p->hbuf,
                     (void *)p->hint, (void *)p->hdbl})
     cudaFree(ptr);
   for (auto *v : {&p->nxg_all, &p->nxg_tiny})
@@ -550,6 +555,30 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     if ((s = plan_groups(p, p->sets[kSetTiny], p->tdesc, tiny_local, work, pos)) != SSPCG_OK) return fail(s);
     if ((e = cudaMemcpy(p->d_work, work.data(), sizeof(int32_t) * nwork, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e));
+    {
+      // problems the FP32 QP-form solves stream (not fully resident): transposed copies of their blocks
+      std::vector<ProbDesc> streamed;
+      for (int32_t i = 0; i < nprob; ++i) {
+        const ProbDesc &d = p->hdesc[i];
+        int K = 0;
+        int64_t b = 0;
+        if (pcg_fit(kOpQp, opts->schedule, d.N, d.nx, d.nu, false, &K, &b) && K < d.N + 1) streamed.push_back(d);
+      }
+      std::vector<int2> sref;
+      for (const ProbDesc &d : streamed)
+        for (int k = 1; k <= d.N; ++k) sref.push_back(make_int2(d.id, k));
+      p->sslots = (int64_t)sref.size();
+      if (p->sslots > 0) {
+        if ((e = upload(&p->d_sref, sref)) != cudaSuccess) return fail(cuda_fail(e));
+        if ((e = cudaMalloc(&p->At, sizeof(float) * std::max<int64_t>(p->sizes[SSPCG_ARRAY_A], 4))) != cudaSuccess)
+          return fail(cuda_fail(e));
+        if ((e = cudaMalloc(&p->Bt, sizeof(float) * std::max<int64_t>(p->sizes[SSPCG_ARRAY_B], 4))) != cudaSuccess)
+          return fail(cuda_fail(e));
+        if ((e = cudaMalloc(&p->PEt, sizeof(float) * std::max<int64_t>(p->sizes[SSPCG_ARRAY_OFF], 4))) !=
+            cudaSuccess)
+          return fail(cuda_fail(e));
+      }
+    }
     if ((e = cudaMalloc(&p->d_counters, sizeof(int32_t) * std::max(1, p->ngroups_total))) != cudaSuccess)
       return fail(cuda_fail(e));
     size_t nside = 0;
@@ -644,6 +673,17 @@ sspcg_status sspcg_build_precond_batched(sspcg_plan *plan, sspcg_precond kind, c
   return SSPCG_OK;
 }
 
+// Transposed A, B, PE for the streamed problems (coalesced reads in the PCG kernel).
+static sspcg_status make_transposes(sspcg_plan *plan, const float *A, const float *B, const float *PE,
+                                    cudaStream_t st) {
+  if (plan->sslots == 0) return SSPCG_OK;
+  const ProbSet ps = plan_set(plan);
+  SSPCG_CUDA(launch_transpose_blocks<float>(ps, plan->d_sref, plan->sslots, 0, A, plan->At, st, device_sms()));
+  if (B) SSPCG_CUDA(launch_transpose_blocks<float>(ps, plan->d_sref, plan->sslots, 1, B, plan->Bt, st, device_sms()));
+  SSPCG_CUDA(launch_transpose_blocks<float>(ps, plan->d_sref, plan->sslots, 2, PE, plan->PEt, st, device_sms()));
+  return SSPCG_OK;
+}
+
 static PcgArgs batched_args(sspcg_plan *plan, const float *A, const float *B, const float *qd, const float *rd,
                             const float *D, const float *E, const void *PD, const void *PE, const float *gamma,
                             float *lambda, int32_t *iters, double *relres, int32_t *status) {
@@ -697,9 +737,10 @@ sspcg_status sspcg_solve_qp_batched(sspcg_plan *plan, const float *A, const floa
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
   plan->build_timed = false;
   time_mark(plan, 1, st);
-  s = launch_sets(plan, {{&plan->sets[kSetQpAll], batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma,
-                                                               lambda, iters, relres, status)}},
-                  st);
+  if ((s = make_transposes(plan, A, B, PE, st)) != SSPCG_OK) return s;
+  PcgArgs a = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
+  if (plan->sslots > 0) { a.At = plan->At; a.Bt = B ? plan->Bt : nullptr; a.PEt = plan->PEt; }
+  s = launch_sets(plan, {{&plan->sets[kSetQpAll], a}}, st);
   time_mark(plan, 2, st);
   return s;
 }
@@ -739,6 +780,7 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
     SSPCG_CUDA(launch_precond_off<double>(tiny_set(plan), plan->d_toref, plan->toff, (int)kind, plan->E64,
                                           plan->PD64, plan->PE64, st, device_sms(), plan->t_offe));
   }
+  if ((s = make_transposes(plan, A, B, PE, st)) != SSPCG_OK) return s;
   plan->build_timed = true;
   time_mark(plan, 1, st);
   PcgArgs a32 = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
@@ -746,6 +788,7 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
   a64.ps = tiny_set(plan);
   a64.PD = plan->PD64;
   a64.PE = plan->PE64;
+  if (plan->sslots > 0) { a32.At = plan->At; a32.Bt = B ? plan->Bt : nullptr; a32.PEt = plan->PEt; }
   s = launch_sets(plan, {{&plan->sets[kSetQpMain], a32}, {&plan->sets[kSetTiny], a64}}, st);
   time_mark(plan, 2, st);
   return s;

@@ -301,6 +301,46 @@ cudaError_t launch_precond_off(const ProbSet &ps, const int2 *refs, int64_t tota
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Block transposes (A_k^T, B_k^T, PE^T) for coalesced reads of streamed rows.
+// which: 0 = A (nx x nx at oA), 1 = B (nx x nu at oB), 2 = off-diagonal
+// preconditioner blocks (nx x nx at ooff).
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kBuildWarps * 32) transpose_kernel(ProbSet ps, const int2 *refs, int64_t nblocks,
+                                                                    int which, const Real *__restrict__ src,
+                                                                    Real *dst) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t g = (int64_t)blockIdx.x * kBuildWarps + wid;
+  if (g >= nblocks) return;
+  const int2 ref = refs ? refs[g] : make_int2(0, (int)g + 1);
+  const ProbDesc d = ps.get(ref.x);
+  const int slot = ref.y - 1;
+  const int rows = d.nx, cols = which == 1 ? d.nu : d.nx;
+  const int64_t base = (which == 0 ? d.oA : which == 1 ? d.oB : d.ooff) + (int64_t)slot * rows * cols;
+  const Real *s = src + base;
+  Real *t = dst + base;
+  // t[c][r] = s[r][c]; writes coalesced by c-major order
+#pragma unroll 4
+  for (int e = lane; e < rows * cols; e += 32) {
+    const int c = e / rows, r = e - c * rows;
+    t[e] = s[r * cols + c];
+  }
+}
+
+template <typename Real>
+cudaError_t launch_transpose_blocks(const ProbSet &ps, const int2 *refs, int64_t nblocks, int which, const Real *src,
+                                    Real *dst, cudaStream_t st, int sms) {
+  if (nblocks == 0) return cudaSuccess;
+  (void)sms;
+  transpose_kernel<Real><<<(unsigned)cdiv(nblocks, kBuildWarps), kBuildWarps * 32, 0, st>>>(ps, refs, nblocks, which,
+                                                                                            src, dst);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_transpose_blocks<float>(const ProbSet &, const int2 *, int64_t, int, const float *,
+                                                    float *, cudaStream_t, int);
+
 template cudaError_t launch_schur_build<float>(const ProbSet &, const int2 *, int64_t, const float *, const float *,
                                                const float *, const float *, float *, float *, cudaStream_t, int);
 template cudaError_t launch_schur_build<double>(const ProbSet &, const int2 *, int64_t, const float *,

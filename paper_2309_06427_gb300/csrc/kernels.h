@@ -80,6 +80,8 @@ struct PcgArgs {
   const float *A, *B, *qd, *rd;  // QP operator data (packed, FP32)
   const float *D, *E;            // block operator data (packed, FP32)
   const void *PD, *PE;           // preconditioner blocks in the working precision
+  const float *At, *Bt;          // optional transposed A_k, B_k (coalesced reads of streamed rows)
+  const void *PEt;               // optional transposed PE blocks
   const float *gamma;
   void *lambda;                  // solution: float when lambda_f32, else the working precision
   int32_t lambda_f32;
@@ -116,6 +118,12 @@ cudaError_t launch_precond_inv(const ProbSet &ps, const int2 *refs, int64_t tota
 template <typename Real>
 cudaError_t launch_precond_off(const ProbSet &ps, const int2 *refs, int64_t total_off, int kind,
                                const Real *E, const Real *PD, Real *PE, cudaStream_t st, int sms, int64_t off_elems);
+// Transpose every block of a packed block array: dst[k] = src[k]^T, blocks of
+// rows x cols with cols = nx and rows = nx (square) or rows = nu (B), one
+// warp per block; refs as for the off-diagonal blocks.
+template <typename Real>
+cudaError_t launch_transpose_blocks(const ProbSet &ps, const int2 *refs, int64_t nblocks, int which, const Real *src,
+                                    Real *dst, cudaStream_t st, int sms);
 cudaError_t launch_residual_qp(const ProbSet &ps, const float *A, const float *B, const float *qd, const float *rd,
                                const float *gamma, const float *lambda, double *relres_true, cudaStream_t st);
 

@@ -107,6 +107,30 @@ __device__ __forceinline__ Real bt_row(const MT *Md, const MT *Mo, int ld, int N
   return acc;
 }
 
+// bt_row from global memory with every access by column: the sub-diagonal
+// block's row i is read as column i of its transpose (Mot), so consecutive
+// rows i of a warp read consecutive addresses.
+template <int NX, typename Real, typename MT>
+__device__ __forceinline__ Real bt_row_t(const MT *Md, const MT *Mo, const MT *Mot, int N, int k, int i,
+                                         const Real *v) {
+  const Real *vk = v + k * NX;
+  const MT *dk = Md + (int64_t)k * NX * NX + i;
+  Real acc = Real(0);
+#pragma unroll
+  for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(dk + j * NX), vk[j], acc);
+  if (k > 0) {
+    const MT *ok = Mot + (int64_t)(k - 1) * NX * NX + i;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(ok + j * NX), vk[j - NX], acc);
+  }
+  if (k < N) {
+    const MT *ok1 = Mo + (int64_t)k * NX * NX + i;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(ok1 + j * NX), vk[NX + j], acc);
+  }
+  return acc;
+}
+
 template <int NX, typename Real>
 __device__ __forceinline__ void stage_blocks(Real *dst, const Real *src, int nblk, int ld, int tid, int T) {
   for (int e = tid; e < nblk * NX * NX; e += T) {
@@ -124,6 +148,8 @@ struct Views {
   const Real *sA, *sB, *sD, *sE, *sPD, *sPE;      // staged (shared memory)
   const float *gA, *gB, *gD, *gE;                 // FP32 inputs (global)
   const Real *gPD, *gPE;                          // preconditioner (global)
+  const float *gAt, *gBt;                         // transposed A_k, B_k (global, optional)
+  const Real *gPEt;                               // transposed PE blocks (global, optional)
   int ld, ldb;                                    // staged row strides
 };
 
@@ -157,6 +183,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   V.ldb = pad_ld(nu > 0 ? nu : 1);
   V.gPD = reinterpret_cast<const Real *>(a.PD) + d.odiag;
   V.gPE = reinterpret_cast<const Real *>(a.PE) + d.ooff;
+  V.gPEt = a.PEt ? reinterpret_cast<const Real *>(a.PEt) + d.ooff : nullptr;
   {
     Real *spd = sm + L.pd, *spe = sm + L.pe;
     stage_blocks<NX>(spd, V.gPD, K, V.ld, tid, T);
@@ -168,6 +195,8 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   if constexpr (OP == kOpQp) {
     V.gA = a.A + d.oA;
     V.gB = a.B + d.oB;
+    V.gAt = a.At ? a.At + d.oA : nullptr;
+    V.gBt = a.Bt ? a.Bt + d.oB : nullptr;
     Real *s0 = sm + L.m0, *s1 = sm + L.m1;
     for (int e = tid; e < Ks * NX * NX; e += T) {
       const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
@@ -251,6 +280,13 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
           for (int j = 0; j < NX; ++j) acc = rfma(Ar[j], vx[j], acc);
           const Real *Br = V.sB + ((k - 1) * NX + i) * V.ldb;
           for (int j = 0; j < nu; ++j) acc = rfma(Br[j], vu[j], acc);
+        } else if (V.gAt) {
+          // row i of A_{k-1} = column i of its transpose: consecutive i are consecutive addresses
+          const float *Ac = V.gAt + (int64_t)(k - 1) * NX * NX + i;
+#pragma unroll
+          for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(Ac + j * NX), vx[j], acc);
+          const float *Bc = V.gBt + (int64_t)(k - 1) * nu * NX + i;
+          for (int j = 0; j < nu; ++j) acc = rfma((Real)__ldg(Bc + j * NX), vu[j], acc);
         } else {
           const float *Ar = V.gA + ((int64_t)(k - 1) * NX + i) * NX;
 #pragma unroll
@@ -266,8 +302,9 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     }
   };
   auto apply_P_row = [&](const Real *src, int k, int i) -> Real {
-    return k < K ? bt_row<NX, true, Real>(V.sPD, V.sPE, V.ld, N, k, i, src)
-                 : bt_row<NX, false, Real>(V.gPD, V.gPE, NX, N, k, i, src);
+    if (k < K) return bt_row<NX, true, Real>(V.sPD, V.sPE, V.ld, N, k, i, src);
+    if (V.gPEt) return bt_row_t<NX, Real>(V.gPD, V.gPE, V.gPEt, N, k, i, src);
+    return bt_row<NX, false, Real>(V.gPD, V.gPE, NX, N, k, i, src);
   };
 
   __syncthreads();  // staged blocks and reciprocals visible
