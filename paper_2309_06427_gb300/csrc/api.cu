@@ -72,10 +72,10 @@ int red_mode(int32_t r) {
 
 int64_t smem_budget() { return (int64_t)max_smem_optin() - kPcgStaticSmem; }  // bytes of dynamic smem
 
-// Threads per CTA for a problem with R rows: about two rows per thread.
+// Threads per CTA for a problem with R rows: one row per thread up to 512.
 int auto_block(int64_t rows) {
-  int64_t t = round_up(cdiv(rows, 2), 32);
-  return (int)std::min<int64_t>(256, std::max<int64_t>(64, t));
+  int64_t t = round_up(rows, 32);
+  return (int)std::min<int64_t>(512, std::max<int64_t>(64, t));
 }
 
 // Staged block rows K and dynamic shared memory (bytes) of a PCG problem
@@ -152,6 +152,8 @@ struct NxGroup {
 
 struct sspcg_plan {
   int32_t nprob = 0;
+  int mx = 1;       // largest nx and nu of the batch
+  int mx_tiny = 1;  // of its FP64 subset
   std::vector<NxGroup> nxg_all, nxg_tiny;
   sspcg_options opts{};
   std::vector<ProbDesc> hdesc;
@@ -167,10 +169,6 @@ struct sspcg_plan {
   int2 *d_tkref = nullptr, *d_toref = nullptr;
   int64_t tknots = 0, toff = 0, t_diag = 0, t_offe = 0;
   double *D64 = nullptr, *E64 = nullptr, *PD64 = nullptr, *PE64 = nullptr;
-  // transposed A, B, PE of the problems that do not fit in shared memory
-  int2 *d_sref = nullptr;  // (problem, block row >= 1) of their off-diagonal slots
-  int64_t sslots = 0;
-  float *At = nullptr, *Bt = nullptr, *PEt = nullptr;
   // PCG launch groups
   int32_t *d_work = nullptr;
   int32_t *d_counters = nullptr;
@@ -198,8 +196,7 @@ void plan_free(sspcg_plan *p) {
   if (p->graph) cudaGraphExecDestroy(p->graph);
   for (void *ptr : {(void *)p->d_desc, (void *)p->d_kref, (void *)p->d_oref, (void *)p->d_tdesc,
                     (void *)p->d_tkref, (void *)p->d_toref, (void *)p->D64, (void *)p->E64,
-                    (void *)p->PD64, (void *)p->PE64, (void *)p->d_sref, (void *)p->At, (void *)p->Bt,
-                    (void *)p->PEt, (void *)p->d_work, (void *)p->d_counters, (void *)p->hbuf,
+                    (void *)p->PD64, (void *)p->PE64, (void *)p->d_work, (void *)p->d_counters, (void *)p->hbuf,
                     (void *)p->hint, (void *)p->hdbl})
     cudaFree(ptr);
   for (auto *v : {&p->nxg_all, &p->nxg_tiny})
@@ -218,22 +215,31 @@ void plan_free(sspcg_plan *p) {
 // group's work list ordered largest first.  ``members`` index ``descs``.
 sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDesc> &descs,
                          const std::vector<int32_t> &members, std::vector<int32_t> &work_host, int32_t &pos) {
-  std::vector<std::vector<int32_t>> buckets(2 * (kMaxNx + 1));
+  // class 0: not fully resident (takes the whole budget); classes 1..3: fully resident within
+  // budget/2, /4, /8 (several CTAs per SM); class 4: the rest of the fully resident problems
+  constexpr int kClasses = 5;
+  std::vector<std::vector<int32_t>> buckets(kClasses * (kMaxNx + 1));
   std::vector<int64_t> bytes(descs.size(), 0);
+  const int64_t budget = smem_budget();
   for (int32_t i : members) {
     const ProbDesc &d = descs[i];
     int K = 0;
     if (!pcg_fit(set.op, p->opts.schedule, d.N, d.nx, d.nu, set.f64, &K, &bytes[i])) return SSPCG_ERR_UNSUPPORTED;
-    buckets[2 * d.nx + (K == d.N + 1 ? 1 : 0)].push_back(i);  // fully resident or not
+    int cls = 0;
+    if (K == d.N + 1) {
+      const int64_t need = bytes[i] + kPcgStaticSmem + 1024;
+      cls = need * 8 <= budget ? 3 : need * 4 <= budget ? 2 : need * 2 <= budget ? 1 : 4;
+    }
+    buckets[kClasses * d.nx + cls].push_back(i);
   }
   for (int nx = 1; nx <= kMaxNx; ++nx) {
-    for (int r = 0; r < 2; ++r) {
-      auto &b = buckets[2 * nx + r];
+    for (int r = 0; r < kClasses; ++r) {
+      auto &b = buckets[kClasses * nx + r];
       if (b.empty()) continue;
       std::stable_sort(b.begin(), b.end(), [&](int32_t x, int32_t y) { return descs[x].N > descs[y].N; });
       PcgGroup g;
       g.nx = nx;
-      g.resident = r == 1;
+      g.resident = r != 0;
       g.f64 = set.f64;
       int64_t maxrows = 0, maxsmem = 0;
       for (int32_t i : b) {
@@ -361,7 +367,8 @@ sspcg_status sspcg_build_schur(int32_t N, int32_t nx, int32_t nu, const float *A
   if (!shape_ok(N, nx, nu)) return SSPCG_ERR_INVALID_ARG;
   if (!qd || !D || (N > 0 && (!A || !rd || !E || (nu > 0 && !B)))) return SSPCG_ERR_INVALID_ARG;
   ProbSet ps{nullptr, single_desc(N, nx, nu), 1};
-  SSPCG_CUDA(launch_schur_build<float>(ps, nullptr, N + 1, A, B, qd, rd, D, E, (cudaStream_t)stream, device_sms()));
+  SSPCG_CUDA(launch_schur_build<float>(ps, nullptr, N + 1, A, B, qd, rd, D, E, (cudaStream_t)stream, device_sms(),
+                                       std::max(nx, nu)));
   return SSPCG_OK;
 }
 
@@ -370,7 +377,8 @@ sspcg_status sspcg_build_schur_f64(int32_t N, int32_t nx, int32_t nu, const floa
   if (!shape_ok(N, nx, nu)) return SSPCG_ERR_INVALID_ARG;
   if (!qd || !D || (N > 0 && (!A || !rd || !E || (nu > 0 && !B)))) return SSPCG_ERR_INVALID_ARG;
   ProbSet ps{nullptr, single_desc(N, nx, nu), 1};
-  SSPCG_CUDA(launch_schur_build<double>(ps, nullptr, N + 1, A, B, qd, rd, D, E, (cudaStream_t)stream, device_sms()));
+  SSPCG_CUDA(launch_schur_build<double>(ps, nullptr, N + 1, A, B, qd, rd, D, E, (cudaStream_t)stream, device_sms(),
+                                        std::max(nx, nu)));
   return SSPCG_OK;
 }
 
@@ -382,7 +390,8 @@ sspcg_status sspcg_build_precond_f64(int32_t N, int32_t nx, sspcg_precond kind, 
   ProbSet ps{nullptr, single_desc(N, nx, 0), 1};
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
   SSPCG_CUDA(launch_precond_inv<double>(ps, nullptr, N + 1, nx, (int)kind, D, PD, status, st));
-  SSPCG_CUDA(launch_precond_off<double>(ps, nullptr, N, (int)kind, E, PD, PE, st, device_sms(), (int64_t)N * nx * nx));
+  SSPCG_CUDA(
+      launch_precond_off<double>(ps, nullptr, N, (int)kind, E, PD, PE, st, device_sms(), (int64_t)N * nx * nx, nx));
   return SSPCG_OK;
 }
 
@@ -394,7 +403,8 @@ sspcg_status sspcg_build_precond(int32_t N, int32_t nx, sspcg_precond kind, cons
   ProbSet ps{nullptr, single_desc(N, nx, 0), 1};
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
   SSPCG_CUDA(launch_precond_inv<float>(ps, nullptr, N + 1, nx, (int)kind, D, PD, status, st));
-  SSPCG_CUDA(launch_precond_off<float>(ps, nullptr, N, (int)kind, E, PD, PE, st, device_sms(), (int64_t)N * nx * nx));
+  SSPCG_CUDA(
+      launch_precond_off<float>(ps, nullptr, N, (int)kind, E, PD, PE, st, device_sms(), (int64_t)N * nx * nx, nx));
   return SSPCG_OK;
 }
 
@@ -494,6 +504,7 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     knot_start[i + 1] = knot_start[i] + n;
     off_start[i + 1] = off_start[i] + Ni;
     all.push_back(i);
+    p->mx = std::max(p->mx, std::max(nx[i], nu[i]));
     const bool f64 = opts->precision == SSPCG_PRECISION_F64 ||
                      (opts->precision == SSPCG_PRECISION_AUTO && n * m <= kTinyUnknowns);
     (f64 ? tiny : main_set).push_back(i);
@@ -512,6 +523,7 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     p->t_diag += round_up(n * m * m, 2);
     p->t_offe += round_up((int64_t)d.N * m * m, 2);
     p->tdesc.push_back(d);
+    p->mx_tiny = std::max(p->mx_tiny, std::max(d.nx, d.nu));
     tknot[t + 1] = tknot[t] + n;
     toff[t + 1] = toff[t] + d.N;
   }
@@ -555,30 +567,6 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     if ((s = plan_groups(p, p->sets[kSetTiny], p->tdesc, tiny_local, work, pos)) != SSPCG_OK) return fail(s);
     if ((e = cudaMemcpy(p->d_work, work.data(), sizeof(int32_t) * nwork, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e));
-    {
-      // problems the FP32 QP-form solves stream (not fully resident): transposed copies of their blocks
-      std::vector<ProbDesc> streamed;
-      for (int32_t i = 0; i < nprob; ++i) {
-        const ProbDesc &d = p->hdesc[i];
-        int K = 0;
-        int64_t b = 0;
-        if (pcg_fit(kOpQp, opts->schedule, d.N, d.nx, d.nu, false, &K, &b) && K < d.N + 1) streamed.push_back(d);
-      }
-      std::vector<int2> sref;
-      for (const ProbDesc &d : streamed)
-        for (int k = 1; k <= d.N; ++k) sref.push_back(make_int2(d.id, k));
-      p->sslots = (int64_t)sref.size();
-      if (p->sslots > 0) {
-        if ((e = upload(&p->d_sref, sref)) != cudaSuccess) return fail(cuda_fail(e));
-        if ((e = cudaMalloc(&p->At, sizeof(float) * std::max<int64_t>(p->sizes[SSPCG_ARRAY_A], 4))) != cudaSuccess)
-          return fail(cuda_fail(e));
-        if ((e = cudaMalloc(&p->Bt, sizeof(float) * std::max<int64_t>(p->sizes[SSPCG_ARRAY_B], 4))) != cudaSuccess)
-          return fail(cuda_fail(e));
-        if ((e = cudaMalloc(&p->PEt, sizeof(float) * std::max<int64_t>(p->sizes[SSPCG_ARRAY_OFF], 4))) !=
-            cudaSuccess)
-          return fail(cuda_fail(e));
-      }
-    }
     if ((e = cudaMalloc(&p->d_counters, sizeof(int32_t) * std::max(1, p->ngroups_total))) != cudaSuccess)
       return fail(cuda_fail(e));
     size_t nside = 0;
@@ -654,7 +642,7 @@ sspcg_status sspcg_build_schur_batched(sspcg_plan *plan, const float *A, const f
   if (!qd || !D || !aligned16(qd) || !aligned16(D)) return SSPCG_ERR_INVALID_ARG;
   if (plan->total_off > 0 && (!A || !rd || !E || !B)) return SSPCG_ERR_INVALID_ARG;
   SSPCG_CUDA(launch_schur_build<float>(plan_set(plan), plan->d_kref, plan->total_knots, A, B, qd, rd, D, E,
-                                       (cudaStream_t)stream, device_sms()));
+                                       (cudaStream_t)stream, device_sms(), plan->mx));
   return SSPCG_OK;
 }
 
@@ -669,18 +657,7 @@ sspcg_status sspcg_build_precond_batched(sspcg_plan *plan, sspcg_precond kind, c
     SSPCG_CUDA(launch_precond_inv<float>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_refs, g.knots, g.nx,
                                          (int)kind, D, PD, status, st));
   SSPCG_CUDA(launch_precond_off<float>(plan_set(plan), plan->d_oref, plan->total_off, (int)kind, E, PD, PE, st,
-                                       device_sms(), plan->sizes[SSPCG_ARRAY_OFF]));
-  return SSPCG_OK;
-}
-
-// Transposed A, B, PE for the streamed problems (coalesced reads in the PCG kernel).
-static sspcg_status make_transposes(sspcg_plan *plan, const float *A, const float *B, const float *PE,
-                                    cudaStream_t st) {
-  if (plan->sslots == 0) return SSPCG_OK;
-  const ProbSet ps = plan_set(plan);
-  SSPCG_CUDA(launch_transpose_blocks<float>(ps, plan->d_sref, plan->sslots, 0, A, plan->At, st, device_sms()));
-  if (B) SSPCG_CUDA(launch_transpose_blocks<float>(ps, plan->d_sref, plan->sslots, 1, B, plan->Bt, st, device_sms()));
-  SSPCG_CUDA(launch_transpose_blocks<float>(ps, plan->d_sref, plan->sslots, 2, PE, plan->PEt, st, device_sms()));
+                                       device_sms(), plan->sizes[SSPCG_ARRAY_OFF], plan->mx));
   return SSPCG_OK;
 }
 
@@ -737,10 +714,9 @@ sspcg_status sspcg_solve_qp_batched(sspcg_plan *plan, const float *A, const floa
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
   plan->build_timed = false;
   time_mark(plan, 1, st);
-  if ((s = make_transposes(plan, A, B, PE, st)) != SSPCG_OK) return s;
-  PcgArgs a = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
-  if (plan->sslots > 0) { a.At = plan->At; a.Bt = B ? plan->Bt : nullptr; a.PEt = plan->PEt; }
-  s = launch_sets(plan, {{&plan->sets[kSetQpAll], a}}, st);
+  s = launch_sets(plan, {{&plan->sets[kSetQpAll], batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma,
+                                                               lambda, iters, relres, status)}},
+                  st);
   time_mark(plan, 2, st);
   return s;
 }
@@ -773,14 +749,13 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
   if ((s = sspcg_build_precond_batched(plan, kind, D, E, PD, PE, status, stream)) != SSPCG_OK) return s;
   if (plan->ntiny > 0) {
     SSPCG_CUDA(launch_schur_build<double>(tiny_set(plan), plan->d_tkref, plan->tknots, A, B, qd, rd, plan->D64,
-                                          plan->E64, st, device_sms()));
+                                          plan->E64, st, device_sms(), plan->mx_tiny));
     for (const NxGroup &g : plan->nxg_tiny)
       SSPCG_CUDA(launch_precond_inv<double>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_refs, g.knots, g.nx,
                                             (int)kind, plan->D64, plan->PD64, status, st));
     SSPCG_CUDA(launch_precond_off<double>(tiny_set(plan), plan->d_toref, plan->toff, (int)kind, plan->E64,
-                                          plan->PD64, plan->PE64, st, device_sms(), plan->t_offe));
+                                          plan->PD64, plan->PE64, st, device_sms(), plan->t_offe, plan->mx_tiny));
   }
-  if ((s = make_transposes(plan, A, B, PE, st)) != SSPCG_OK) return s;
   plan->build_timed = true;
   time_mark(plan, 1, st);
   PcgArgs a32 = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
@@ -788,7 +763,7 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
   a64.ps = tiny_set(plan);
   a64.PD = plan->PD64;
   a64.PE = plan->PE64;
-  if (plan->sslots > 0) { a32.At = plan->At; a32.Bt = B ? plan->Bt : nullptr; a32.PEt = plan->PEt; }
+
   s = launch_sets(plan, {{&plan->sets[kSetQpMain], a32}, {&plan->sets[kSetTiny], a64}}, st);
   time_mark(plan, 2, st);
   return s;

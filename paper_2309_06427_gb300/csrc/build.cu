@@ -8,7 +8,7 @@
 
 namespace sspcg {
 
-constexpr int kBuildWarps = 4;  // warps per CTA of the build kernels
+constexpr int kBuildWarps = 8;  // warps per CTA of the build kernels
 
 // ---------------------------------------------------------------------------
 // K1: D_k, E_k from (A, B, diag Q, diag R).
@@ -17,23 +17,24 @@ constexpr int kBuildWarps = 4;  // warps per CTA of the build kernels
 //   E[k-1] = S(k, k-1) = -A_{k-1} Q_{k-1}^-1                                   (= -phi_{k-1})
 // Real = float (FP32 arithmetic) or double (the FP64 path); only the upper
 // triangle of D_k is summed and mirrored, so D_k is exactly symmetric.
-// Shared memory per warp: AQ (nx*nx), A (nx*nx), BR (nx*nu), B (nx*nu), 1/q_k (nx).
+// Shared memory per warp: AQ, A, BR, B (mx*mx each, mx = largest nx, nu of the launch), 1/q_k (mx).
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(kBuildWarps * 32) schur_build_kernel(ProbSet ps, const int2 *refs,
                                                                       int64_t total_knots, const float *__restrict__ A,
                                                                       const float *__restrict__ B,
                                                                       const float *__restrict__ qd,
-                                                                      const float *__restrict__ rd, Real *D, Real *E) {
+                                                                      const float *__restrict__ rd, Real *D, Real *E,
+                                                                      int mx) {
   extern __shared__ float4 smem_raw[];
   Real *smem = reinterpret_cast<Real *>(smem_raw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int per_warp = 2 * kMaxNx * kMaxNx + 2 * kMaxNx * kMaxNx + kMaxNx;
+  const int per_warp = 4 * mx * mx + mx;  // mx: largest nx (and nu) of the launch
   Real *sAQ = smem + wid * per_warp;
-  Real *sA = sAQ + kMaxNx * kMaxNx;
-  Real *sBR = sA + kMaxNx * kMaxNx;
-  Real *sB = sBR + kMaxNx * kMaxNx;
-  Real *sIq = sB + kMaxNx * kMaxNx;
+  Real *sA = sAQ + mx * mx;
+  Real *sBR = sA + mx * mx;
+  Real *sB = sBR + mx * mx;
+  Real *sIq = sB + mx * mx;
   for (int64_t g = (int64_t)blockIdx.x * kBuildWarps + wid; g < total_knots; g += (int64_t)gridDim.x * kBuildWarps) {
     const int2 ref = refs ? refs[g] : make_int2(0, (int)g);  // (problem, block row)
     const ProbDesc d = ps.get(ref.x);
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int2
     for (int i = nx - 1; i > j; --i) {
       double *Mi = M + tri(i, 0);
       const double lij = Mi[j] * inv;
+#pragma unroll 4
       for (int c = j + 1; c <= i; ++c) Mi[c] = fma(-lij, M[tri(c, j)], Mi[c]);
       Mi[j] = lij;
     }
@@ -160,20 +162,31 @@ __global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int2
   for (int j = 0; j + 1 < nx; ++j) {
     for (int i = j + 1; i < nx; ++i) {
       const double *Mi = M + tri(i, 0);
-      double s = Mi[j];
-      for (int t = j + 1; t < i; ++t) s = fma(Mi[t], M[tri(t, j)], s);
-      M[tri(i, j)] = -s;
+      double s0 = Mi[j], s1 = 0.0;  // two chains
+      int t = j + 1;
+      for (; t + 1 < i; t += 2) {
+        s0 = fma(Mi[t], M[tri(t, j)], s0);
+        s1 = fma(Mi[t + 1], M[tri(t + 1, j)], s1);
+      }
+      if (t < i) s0 = fma(Mi[t], M[tri(t, j)], s0);
+      M[tri(i, j)] = -(s0 + s1);
     }
   }
   // D^-1 = W^T diag(1/d) W, lower triangle, mirrored.
   for (int i = 0; i < nx; ++i) {
     for (int j = 0; j <= i; ++j) {
-      double s = M[tri(i, i)] * (i == j ? 1.0 : M[tri(i, j)]);
-      for (int t = i + 1; t < nx; ++t) {
-        const double *Mt = M + tri(t, 0);
-        s = fma(Mt[i] * Mt[t], Mt[j], s);
+      double s0 = M[tri(i, i)] * (i == j ? 1.0 : M[tri(i, j)]), s1 = 0.0;  // two chains
+      int t = i + 1;
+      for (; t + 1 < nx; t += 2) {
+        const double *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
+        s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
+        s1 = fma(Mu[i] * Mu[t + 1], Mu[j], s1);
       }
-      const Real f = (Real)s;
+      if (t < nx) {
+        const double *Mt = M + tri(t, 0);
+        s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
+      }
+      const Real f = (Real)(s0 + s1);
       PDk[i * nx + j] = f;
       PDk[j * nx + i] = f;
     }
@@ -183,21 +196,21 @@ __global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int2
 // ---------------------------------------------------------------------------
 // K2b: PE[k-1] = -c * PD_k E[k-1] PD_{k-1}, c = 1 (symmetric stair) or 1/2
 // (additive stair), in Real.  One warp per off-diagonal block.
-// Shared memory per warp: PD_k, E, PD_{k-1}, T = PD_k E (4 * nx * nx floats).
+// Shared memory per warp: PD_k, E, PD_{k-1}, T = PD_k E (4 * mx * mx elements).
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(kBuildWarps * 32) precond_off_kernel(ProbSet ps, const int2 *refs,
                                                                       int64_t total_off, Real c,
                                                                       const Real *__restrict__ E,
-                                                                      const Real *__restrict__ PD, Real *PE) {
+                                                                      const Real *__restrict__ PD, Real *PE, int mx) {
   extern __shared__ float4 smem_raw[];
   Real *smem = reinterpret_cast<Real *>(smem_raw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int per_warp = 4 * kMaxNx * kMaxNx;
+  const int per_warp = 4 * mx * mx;  // mx: largest nx of the launch
   Real *sP1 = smem + wid * per_warp;
-  Real *sE = sP1 + kMaxNx * kMaxNx;
-  Real *sP0 = sE + kMaxNx * kMaxNx;
-  Real *sT = sP0 + kMaxNx * kMaxNx;
+  Real *sE = sP1 + mx * mx;
+  Real *sP0 = sE + mx * mx;
+  Real *sT = sP0 + mx * mx;
   for (int64_t g = (int64_t)blockIdx.x * kBuildWarps + wid; g < total_off; g += (int64_t)gridDim.x * kBuildWarps) {
     const int2 ref = refs ? refs[g] : make_int2(0, (int)g + 1);  // (problem, block row k >= 1)
     const ProbDesc d = ps.get(ref.x);
@@ -235,26 +248,28 @@ __global__ void __launch_bounds__(kBuildWarps * 32) precond_off_kernel(ProbSet p
 // Launch helpers
 // ---------------------------------------------------------------------------
 static int build_grid(int64_t items, int sms) {
-  const int64_t need = cdiv(items, kBuildWarps);
-  const int64_t cap = (int64_t)sms * 8;
+  (void)sms;
+  const int64_t need = cdiv(items, kBuildWarps);  // one warp per item
+  const int64_t cap = 1 << 30;
   return (int)(need < cap ? (need < 1 ? 1 : need) : cap);
 }
 
 template <typename Real>
 cudaError_t launch_schur_build(const ProbSet &ps, const int2 *refs, int64_t total_knots, const float *A,
                                const float *B, const float *qd, const float *rd, Real *D, Real *E,
-                               cudaStream_t st, int sms) {
+                               cudaStream_t st, int sms, int mx) {
   if (total_knots == 0) return cudaSuccess;
-  const size_t smem = sizeof(Real) * kBuildWarps * (4 * kMaxNx * kMaxNx + kMaxNx);
+  const size_t smem = sizeof(Real) * kBuildWarps * (4 * mx * mx + mx);
   static bool attr = false;
   if (!attr) {
+    const size_t most = sizeof(Real) * kBuildWarps * (4 * kMaxNx * kMaxNx + kMaxNx);
     cudaError_t e =
-        cudaFuncSetAttribute(schur_build_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(schur_build_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   schur_build_kernel<Real><<<build_grid(total_knots, sms), kBuildWarps * 32, smem, st>>>(ps, refs, total_knots,
-                                                                                          A, B, qd, rd, D, E);
+                                                                                          A, B, qd, rd, D, E, mx);
   return cudaGetLastError();
 }
 
@@ -282,77 +297,40 @@ cudaError_t launch_precond_inv(const ProbSet &ps, const int2 *refs, int64_t tota
 
 template <typename Real>
 cudaError_t launch_precond_off(const ProbSet &ps, const int2 *refs, int64_t total_off, int kind,
-                               const Real *E, const Real *PD, Real *PE, cudaStream_t st, int sms, int64_t off_elems) {
+                               const Real *E, const Real *PD, Real *PE, cudaStream_t st, int sms, int64_t off_elems,
+                               int mx) {
   if (total_off == 0) return cudaSuccess;
   if (kind == 2 || kind == 3) {  // block-Jacobi, Jacobi: no off-diagonal blocks
     return cudaMemsetAsync(PE, 0, sizeof(Real) * off_elems, st);
   }
-  const size_t smem_o = sizeof(Real) * kBuildWarps * (4 * kMaxNx * kMaxNx);
+  const size_t smem_o = sizeof(Real) * kBuildWarps * (4 * mx * mx);
   static bool attr = false;
   if (!attr) {
+    const size_t most = sizeof(Real) * kBuildWarps * (4 * kMaxNx * kMaxNx);
     cudaError_t e =
-        cudaFuncSetAttribute(precond_off_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_o);
+        cudaFuncSetAttribute(precond_off_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const Real c = (kind == 0) ? Real(1) : Real(0.5);
   precond_off_kernel<Real><<<build_grid(total_off, sms), kBuildWarps * 32, smem_o, st>>>(ps, refs, total_off, c,
-                                                                                          E, PD, PE);
+                                                                                          E, PD, PE, mx);
   return cudaGetLastError();
 }
-
-// ---------------------------------------------------------------------------
-// Block transposes (A_k^T, B_k^T, PE^T) for coalesced reads of streamed rows.
-// which: 0 = A (nx x nx at oA), 1 = B (nx x nu at oB), 2 = off-diagonal
-// preconditioner blocks (nx x nx at ooff).
-// ---------------------------------------------------------------------------
-template <typename Real>
-__global__ void __launch_bounds__(kBuildWarps * 32) transpose_kernel(ProbSet ps, const int2 *refs, int64_t nblocks,
-                                                                    int which, const Real *__restrict__ src,
-                                                                    Real *dst) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t g = (int64_t)blockIdx.x * kBuildWarps + wid;
-  if (g >= nblocks) return;
-  const int2 ref = refs ? refs[g] : make_int2(0, (int)g + 1);
-  const ProbDesc d = ps.get(ref.x);
-  const int slot = ref.y - 1;
-  const int rows = d.nx, cols = which == 1 ? d.nu : d.nx;
-  const int64_t base = (which == 0 ? d.oA : which == 1 ? d.oB : d.ooff) + (int64_t)slot * rows * cols;
-  const Real *s = src + base;
-  Real *t = dst + base;
-  // t[c][r] = s[r][c]; writes coalesced by c-major order
-#pragma unroll 4
-  for (int e = lane; e < rows * cols; e += 32) {
-    const int c = e / rows, r = e - c * rows;
-    t[e] = s[r * cols + c];
-  }
-}
-
-template <typename Real>
-cudaError_t launch_transpose_blocks(const ProbSet &ps, const int2 *refs, int64_t nblocks, int which, const Real *src,
-                                    Real *dst, cudaStream_t st, int sms) {
-  if (nblocks == 0) return cudaSuccess;
-  (void)sms;
-  transpose_kernel<Real><<<(unsigned)cdiv(nblocks, kBuildWarps), kBuildWarps * 32, 0, st>>>(ps, refs, nblocks, which,
-                                                                                            src, dst);
-  return cudaGetLastError();
-}
-
-template cudaError_t launch_transpose_blocks<float>(const ProbSet &, const int2 *, int64_t, int, const float *,
-                                                    float *, cudaStream_t, int);
 
 template cudaError_t launch_schur_build<float>(const ProbSet &, const int2 *, int64_t, const float *, const float *,
-                                               const float *, const float *, float *, float *, cudaStream_t, int);
+                                               const float *, const float *, float *, float *, cudaStream_t, int,
+                                               int);
 template cudaError_t launch_schur_build<double>(const ProbSet &, const int2 *, int64_t, const float *,
                                                 const float *, const float *, const float *, double *, double *,
-                                                cudaStream_t, int);
+                                                cudaStream_t, int, int);
 template cudaError_t launch_precond_inv<float>(const ProbSet &, const int2 *, int64_t, int, int, const float *,
                                                float *, int32_t *, cudaStream_t);
 template cudaError_t launch_precond_inv<double>(const ProbSet &, const int2 *, int64_t, int, int, const double *,
                                                 double *, int32_t *, cudaStream_t);
 template cudaError_t launch_precond_off<float>(const ProbSet &, const int2 *, int64_t, int, const float *,
-                                               const float *, float *, cudaStream_t, int, int64_t);
+                                               const float *, float *, cudaStream_t, int, int64_t, int);
 template cudaError_t launch_precond_off<double>(const ProbSet &, const int2 *, int64_t, int, const double *,
-                                                const double *, double *, cudaStream_t, int, int64_t);
+                                                const double *, double *, cudaStream_t, int, int64_t, int);
 
 }  // namespace sspcg

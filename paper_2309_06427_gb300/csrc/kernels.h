@@ -29,22 +29,27 @@ struct PcgLayout {
   int64_t total;
 };
 
+// Vectors are stored with a block-row stride of nx rounded up to 4 elements,
+// so that every block row starts 16-byte aligned and a thread can load a
+// whole block-row segment with 128-bit loads.
+__host__ __device__ __forceinline__ int vec_stride(int x) { return (x + 3) & ~3; }
+
 __host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, int nu) {
   PcgLayout L{};
-  const int64_t n = N + 1, R4 = round_up(n * nx, 4);
+  const int64_t n = N + 1, NXP = vec_stride(nx), NUP = vec_stride(nu), RV = n * NXP;
   const int64_t Ks = K < N ? K : N;  // staged off-diagonal slots
   const int64_t ld = pad_ld(nx), ldb = pad_ld(nu > 0 ? nu : 1);
   int64_t o = 0;
-  L.p = o; o += R4;
-  L.r = o; o += R4;
-  L.w = o; o += R4;
-  L.x = o; o += R4;
+  L.p = o; o += RV;
+  L.r = o; o += RV;
+  L.w = o; o += RV;
+  L.x = o; o += RV;
   L.v = o;
-  if (op == kOpQp) o += round_up(n * nx + (int64_t)N * nu, 4);
+  if (op == kOpQp) o += RV + (int64_t)N * NUP;   // v_x then v_u
   L.iq = o;
-  if (op == kOpQp) o += round_up(n * nx, 4);
+  if (op == kOpQp) o += RV;
   L.ir = o;
-  if (op == kOpQp) o += round_up((int64_t)N * nu, 4);
+  if (op == kOpQp) o += (int64_t)N * NUP;
   if (op == kOpQp) {
     L.m0 = o; o += round_up(Ks * nx * ld, 4);    // A_k, row stride ld
     L.m1 = o; o += round_up(Ks * nx * ldb, 4);   // B_k, row stride ldb
@@ -80,8 +85,6 @@ struct PcgArgs {
   const float *A, *B, *qd, *rd;  // QP operator data (packed, FP32)
   const float *D, *E;            // block operator data (packed, FP32)
   const void *PD, *PE;           // preconditioner blocks in the working precision
-  const float *At, *Bt;          // optional transposed A_k, B_k (coalesced reads of streamed rows)
-  const void *PEt;               // optional transposed PE blocks
   const float *gamma;
   void *lambda;                  // solution: float when lambda_f32, else the working precision
   int32_t lambda_f32;
@@ -105,10 +108,11 @@ int pcg_max_smem_bytes();
 // Schur build and preconditioner assembly; Real = float (FP32 blocks) or
 // double (the FP64 path).  refs[i] = (problem, block row) of work item i
 // (nullptr: one problem, item i is block row i, or i + 1 for off-diagonals).
+// mx: the largest nx and nu of the launch (sizes the per-warp shared memory).
 template <typename Real>
 cudaError_t launch_schur_build(const ProbSet &ps, const int2 *refs, int64_t total_knots, const float *A,
                                const float *B, const float *qd, const float *rd, Real *D, Real *E,
-                               cudaStream_t st, int sms);
+                               cudaStream_t st, int sms, int mx);
 // Diagonal blocks of Phi^-1 (FP64 inverses), one thread per knot: every
 // knot of a launch must have the same nx.
 template <typename Real>
@@ -117,13 +121,8 @@ cudaError_t launch_precond_inv(const ProbSet &ps, const int2 *refs, int64_t tota
 // Off-diagonal blocks of Phi^-1 (any mix of nx).
 template <typename Real>
 cudaError_t launch_precond_off(const ProbSet &ps, const int2 *refs, int64_t total_off, int kind,
-                               const Real *E, const Real *PD, Real *PE, cudaStream_t st, int sms, int64_t off_elems);
-// Transpose every block of a packed block array: dst[k] = src[k]^T, blocks of
-// rows x cols with cols = nx and rows = nx (square) or rows = nu (B), one
-// warp per block; refs as for the off-diagonal blocks.
-template <typename Real>
-cudaError_t launch_transpose_blocks(const ProbSet &ps, const int2 *refs, int64_t nblocks, int which, const Real *src,
-                                    Real *dst, cudaStream_t st, int sms);
+                               const Real *E, const Real *PD, Real *PE, cudaStream_t st, int sms, int64_t off_elems,
+                               int mx);
 cudaError_t launch_residual_qp(const ProbSet &ps, const float *A, const float *B, const float *qd, const float *rd,
                                const float *gamma, const float *lambda, double *relres_true, cudaStream_t st);
 

@@ -4,7 +4,10 @@
 // instantiation units.
 //
 // Thread mapping: thread t owns rows t, t + T, t + 2T, ... of the
-// (N+1)*nx unknowns; row = k*nx + i is row i of block row k.
+// (N+1)*nx unknowns; row = k*nx + i is row i of block row k.  Vectors live
+// in shared memory with a block-row stride of nx rounded up to 4, and each
+// row loads the block-row segments it multiplies into registers with
+// 128-bit loads.
 //
 // Per iteration (textbook PCG, Saad Alg. 9.1):
 //   w = S p                 (QP form: v = G^-1 C^T p, barrier, w = C v)
@@ -13,6 +16,10 @@
 //   z = Phi^-1 r, (r.z), (r.r) block reduction
 //   beta = (r.z)new / (r.z)old, p = z + beta p, barrier
 // Stop before an iteration once r.r <= tol^2 gamma.gamma.
+//
+// The first K block rows of the operator and preconditioner blocks are
+// staged in shared memory (odd row strides); the rest are read from global
+// memory every iteration (L1/L2).
 //
 // Real is the working precision (float: the fast path; double: the FP64
 // path).  The QP data A, B, diag Q, diag R and gamma are FP32 inputs in both
@@ -83,50 +90,59 @@ __device__ __forceinline__ void block_sum(typename R::T (&v)[K], typename R::T *
   for (int e = 0; e < K; ++e) v[e] = R::sum(lane < nw ? slots[e * 32 + lane] : R::zero());
 }
 
-// Row (k, i) of a block-tridiagonal symmetric matrix times v:
-//   Md: diagonal blocks (symmetric; read by column so that consecutive i are
-//   consecutive addresses), Mo: sub-diagonal blocks, Mo[k-1] = M(k, k-1),
-//   M(k, k+1) = Mo[k]^T.  ld: row stride of the blocks.
-template <int NX, bool RES, typename Real, typename MT>
-__device__ __forceinline__ Real bt_row(const MT *Md, const MT *Mo, int ld, int N, int k, int i, const Real *v) {
-  const Real *vk = v + k * NX;
-  const MT *dk = Md + (int64_t)k * NX * ld + i;
-  Real acc = Real(0);
+// A block-row segment of a vector in registers: NXP = nx rounded up to 4
+// entries, loaded with 128-bit shared-memory loads (the segment starts
+// 16-byte aligned; entries past nx are padding and never used).
+template <int NX, typename Real>
+struct Seg {
+  static constexpr int NXP = (NX + 3) & ~3;
+  Real v[NXP];
+  __device__ __forceinline__ void load(const Real *src) {
+    constexpr int per = 16 / (int)sizeof(Real);
 #pragma unroll
-  for (int j = 0; j < NX; ++j) acc = rfma((Real)ldm<RES>(dk + j * ld), vk[j], acc);
-  if (k > 0) {
-    const MT *ok = Mo + (int64_t)(k - 1) * NX * ld + i * ld;
-#pragma unroll
-    for (int j = 0; j < NX; ++j) acc = rfma((Real)ldm<RES>(ok + j), vk[j - NX], acc);
+    for (int q = 0; q < NXP / per; ++q) {
+      const float4 c = reinterpret_cast<const float4 *>(src)[q];
+      if constexpr (sizeof(Real) == 4) {
+        v[4 * q + 0] = c.x; v[4 * q + 1] = c.y; v[4 * q + 2] = c.z; v[4 * q + 3] = c.w;
+      } else {
+        const double2 dd = *reinterpret_cast<const double2 *>(&c);
+        v[2 * q + 0] = dd.x; v[2 * q + 1] = dd.y;
+      }
+    }
   }
-  if (k < N) {
-    const MT *ok1 = Mo + (int64_t)k * NX * ld + i;
+};
+
+// sum_{j < NX} m[j * stride] * seg[j] with two independent accumulators
+// (even and odd j), so that consecutive FMAs do not wait on each other.
+template <int NX, bool SMEM, typename Real, typename MT>
+__device__ __forceinline__ Real dot_seg(const MT *m, int stride, const Real *seg) {
+  Real a0 = Real(0), a1 = Real(0);
 #pragma unroll
-    for (int j = 0; j < NX; ++j) acc = rfma((Real)ldm<RES>(ok1 + j * ld), vk[NX + j], acc);
+  for (int j = 0; j < NX; j += 2) {
+    a0 = rfma((Real)ldm<SMEM>(m + j * stride), seg[j], a0);
+    if (j + 1 < NX) a1 = rfma((Real)ldm<SMEM>(m + (j + 1) * stride), seg[j + 1], a1);
   }
-  return acc;
+  return a0 + a1;
 }
 
-// bt_row from global memory with every access by column: the sub-diagonal
-// block's row i is read as column i of its transpose (Mot), so consecutive
-// rows i of a warp read consecutive addresses.
-template <int NX, typename Real, typename MT>
-__device__ __forceinline__ Real bt_row_t(const MT *Md, const MT *Mo, const MT *Mot, int N, int k, int i,
-                                         const Real *v) {
-  const Real *vk = v + k * NX;
-  const MT *dk = Md + (int64_t)k * NX * NX + i;
-  Real acc = Real(0);
-#pragma unroll
-  for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(dk + j * NX), vk[j], acc);
+// Row (k, i) of a block-tridiagonal symmetric matrix times v (block-row
+// stride NXP): Md diagonal blocks (symmetric; read by column so that
+// consecutive i are consecutive addresses), Mo sub-diagonal blocks with
+// Mo[k-1] = M(k, k-1) (read by row), and M(k, k+1) = Mo[k]^T (read by
+// column).  ld: row stride.
+template <int NX, bool SMEM, typename Real, typename MT>
+__device__ __forceinline__ Real bt_row(const MT *Md, const MT *Mo, int ld, int N, int k, int i, const Real *v) {
+  constexpr int NXP = (NX + 3) & ~3;
+  Seg<NX, Real> s;
+  s.load(v + k * NXP);
+  Real acc = dot_seg<NX, SMEM, Real>(Md + (int64_t)k * NX * ld + i, ld, s.v);
   if (k > 0) {
-    const MT *ok = Mot + (int64_t)(k - 1) * NX * NX + i;
-#pragma unroll
-    for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(ok + j * NX), vk[j - NX], acc);
+    s.load(v + (k - 1) * NXP);
+    acc += dot_seg<NX, SMEM, Real>(Mo + ((int64_t)(k - 1) * NX + i) * ld, 1, s.v);
   }
   if (k < N) {
-    const MT *ok1 = Mo + (int64_t)k * NX * NX + i;
-#pragma unroll
-    for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(ok1 + j * NX), vk[NX + j], acc);
+    s.load(v + (k + 1) * NXP);
+    acc += dot_seg<NX, SMEM, Real>(Mo + (int64_t)k * NX * ld + i, ld, s.v);
   }
   return acc;
 }
@@ -148,8 +164,6 @@ struct Views {
   const Real *sA, *sB, *sD, *sE, *sPD, *sPE;      // staged (shared memory)
   const float *gA, *gB, *gD, *gE;                 // FP32 inputs (global)
   const Real *gPD, *gPE;                          // preconditioner (global)
-  const float *gAt, *gBt;                         // transposed A_k, B_k (global, optional)
-  const Real *gPEt;                               // transposed PE blocks (global, optional)
   int ld, ldb;                                    // staged row strides
 };
 
@@ -157,8 +171,9 @@ template <int NX, int OP, int RED, typename Real>
 __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typename Red<RED, Real>::T *slots) {
   using R = Red<RED, Real>;
   using AccT = typename R::T;
+  constexpr int NXP = (NX + 3) & ~3;
   const int p = d.id;  // output slot
-  const int N = d.N, n = N + 1, nu = d.nu, R_ = n * NX;
+  const int N = d.N, n = N + 1, nu = d.nu, R_ = n * NX, NUP = vec_stride(nu);
   const int tid = threadIdx.x, T = blockDim.x;
   int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems);  // the host sized smem so that K >= 0
   if (K > a.max_resident) K = a.max_resident;
@@ -166,6 +181,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   const int Ks = K < N ? K : N;
   const PcgLayout L = pcg_layout(OP, K, N, NX, nu);
   Real *sp = sm + L.p, *sr = sm + L.r, *sw = sm + L.w, *sx = sm + L.x, *sv = sm + L.v;
+  Real *svu = sv + n * NXP;  // v_u block rows, stride NUP
   const float *gam = a.gamma + d.ovec;
   // lambda (global): read once for a warm start, written once at the end
   auto lam_load = [&](int row) -> Real {
@@ -176,6 +192,12 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     if (a.lambda_f32) reinterpret_cast<float *>(a.lambda)[d.ovec + row] = (float)v;
     else reinterpret_cast<Real *>(a.lambda)[d.ovec + row] = v;
   };
+  // storage index of row (k, i) in the strided vectors
+  auto vid = [&](int row, int &k, int &i) {
+    k = row / NX;
+    i = row - k * NX;
+    return k * NXP + i;
+  };
 
   // ---- views and staging ----
   Views<Real> V{};
@@ -183,7 +205,6 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   V.ldb = pad_ld(nu > 0 ? nu : 1);
   V.gPD = reinterpret_cast<const Real *>(a.PD) + d.odiag;
   V.gPE = reinterpret_cast<const Real *>(a.PE) + d.ooff;
-  V.gPEt = a.PEt ? reinterpret_cast<const Real *>(a.PEt) + d.ooff : nullptr;
   {
     Real *spd = sm + L.pd, *spe = sm + L.pe;
     stage_blocks<NX>(spd, V.gPD, K, V.ld, tid, T);
@@ -195,8 +216,6 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   if constexpr (OP == kOpQp) {
     V.gA = a.A + d.oA;
     V.gB = a.B + d.oB;
-    V.gAt = a.At ? a.At + d.oA : nullptr;
-    V.gBt = a.Bt ? a.Bt + d.oB : nullptr;
     Real *s0 = sm + L.m0, *s1 = sm + L.m1;
     for (int e = tid; e < Ks * NX * NX; e += T) {
       const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
@@ -206,8 +225,14 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       const int row = e / nu, c = e - row * nu;
       s1[row * V.ldb + c] = (Real)V.gB[e];
     }
-    for (int e = tid; e < n * NX; e += T) siq[e] = Real(1) / (Real)gq[e];
-    for (int e = tid; e < N * nu; e += T) sir[e] = Real(1) / (Real)gr[e];
+    for (int e = tid; e < R_; e += T) {
+      const int k = e / NX, j = e - k * NX;
+      siq[k * NXP + j] = Real(1) / (Real)gq[e];
+    }
+    for (int e = tid; e < N * nu; e += T) {
+      const int k = e / nu, j = e - k * nu;
+      sir[k * NUP + j] = Real(1) / (Real)gr[e];
+    }
     V.sA = s0; V.sB = s1;
   } else {
     V.gD = a.D + d.odiag;
@@ -225,75 +250,58 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   }
 
   // QP form, phase 1: sv = G^-1 C^T src (all threads), then a barrier.
+  //   v_x(k)[j] = (-src_k[j] + sum_l A_k[l][j] src_{k+1}[l]) / q_k[j]
+  //   v_u(k)[j] = (sum_l B_k[l][j] src_{k+1}[l]) / r_k[j]
   auto apply_S_phase1 = [&](const Real *src) {
     if constexpr (OP == kOpQp) {
-      const int nvx = n * NX, nitems = nvx + N * nu;
+      const int nitems = R_ + N * nu;
       const float inv_nu = nu > 0 ? 1.0f / (float)nu : 0.0f;
       for (int it = tid; it < nitems; it += T) {
-        if (it < nvx) {
+        if (it < R_) {
           const int k = it / NX, j = it - k * NX;
-          Real acc = -src[it];
+          Real acc = -src[k * NXP + j];
           if (k < N) {
-            const Real *pk1 = src + (k + 1) * NX;
-            if (k < K) {
-              const Real *Ak = V.sA + k * NX * V.ld + j;  // column j of A_k (staged)
-#pragma unroll
-              for (int l = 0; l < NX; ++l) acc = rfma(Ak[l * V.ld], pk1[l], acc);
-            } else {
-              const float *Ak = V.gA + (int64_t)k * NX * NX + j;
-#pragma unroll
-              for (int l = 0; l < NX; ++l) acc = rfma((Real)__ldg(Ak + l * NX), pk1[l], acc);
-            }
+            Seg<NX, Real> s;
+            s.load(src + (k + 1) * NXP);
+            if (k < K) acc += dot_seg<NX, true, Real>(V.sA + k * NX * V.ld + j, V.ld, s.v);
+            else acc += dot_seg<NX, false, Real>(V.gA + (int64_t)k * NX * NX + j, NX, s.v);
           }
-          sv[it] = acc * siq[it];
+          sv[k * NXP + j] = acc * siq[k * NXP + j];
         } else {
-          const int t2 = it - nvx;
+          const int t2 = it - R_;
           const int k = (int)(((float)t2 + 0.5f) * inv_nu);
           const int j = t2 - k * nu;
-          const Real *pk1 = src + (k + 1) * NX;
-          Real acc = Real(0);
-          if (k < K) {
-            const Real *Bk = V.sB + k * NX * V.ldb + j;  // column j of B_k (staged)
-#pragma unroll
-            for (int l = 0; l < NX; ++l) acc = rfma(Bk[l * V.ldb], pk1[l], acc);
-          } else {
-            const float *Bk = V.gB + (int64_t)k * NX * nu + j;
-#pragma unroll
-            for (int l = 0; l < NX; ++l) acc = rfma((Real)__ldg(Bk + l * nu), pk1[l], acc);
-          }
-          sv[it] = acc * sir[t2];
+          Seg<NX, Real> s;
+          s.load(src + (k + 1) * NXP);
+          Real acc;
+          if (k < K) acc = dot_seg<NX, true, Real>(V.sB + k * NX * V.ldb + j, V.ldb, s.v);
+          else acc = dot_seg<NX, false, Real>(V.gB + (int64_t)k * NX * nu + j, nu, s.v);
+          svu[k * NUP + j] = acc * sir[k * NUP + j];
         }
       }
       __syncthreads();
     }
   };
   // Row (k, i) of S src (QP form: of C sv).
+  //   w_k[i] = -v_x(k)[i] + A_{k-1}[i,:] v_x(k-1) + B_{k-1}[i,:] v_u(k-1)
   auto apply_S_row = [&](const Real *src, int k, int i) -> Real {
     if constexpr (OP == kOpQp) {
-      Real acc = -sv[k * NX + i];
+      Real acc = -sv[k * NXP + i];
       if (k > 0) {
-        const Real *vx = sv + (k - 1) * NX;
-        const Real *vu = sv + n * NX + (k - 1) * nu;
+        Seg<NX, Real> s;
+        s.load(sv + (k - 1) * NXP);
+        const Real *vu = svu + (k - 1) * NUP;
+        Real ab = Real(0);
         if (k < K) {
-          const Real *Ar = V.sA + ((k - 1) * NX + i) * V.ld;  // row i of A_{k-1}
-#pragma unroll
-          for (int j = 0; j < NX; ++j) acc = rfma(Ar[j], vx[j], acc);
+          acc += dot_seg<NX, true, Real>(V.sA + ((k - 1) * NX + i) * V.ld, 1, s.v);
           const Real *Br = V.sB + ((k - 1) * NX + i) * V.ldb;
-          for (int j = 0; j < nu; ++j) acc = rfma(Br[j], vu[j], acc);
-        } else if (V.gAt) {
-          // row i of A_{k-1} = column i of its transpose: consecutive i are consecutive addresses
-          const float *Ac = V.gAt + (int64_t)(k - 1) * NX * NX + i;
-#pragma unroll
-          for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(Ac + j * NX), vx[j], acc);
-          const float *Bc = V.gBt + (int64_t)(k - 1) * nu * NX + i;
-          for (int j = 0; j < nu; ++j) acc = rfma((Real)__ldg(Bc + j * NX), vu[j], acc);
+          for (int j = 0; j < nu; ++j) ab = rfma(Br[j], vu[j], ab);
         } else {
-          const float *Ar = V.gA + ((int64_t)(k - 1) * NX + i) * NX;
-#pragma unroll
-          for (int j = 0; j < NX; ++j) acc = rfma((Real)__ldg(Ar + j), vx[j], acc);
+          acc += dot_seg<NX, false, Real>(V.gA + ((int64_t)(k - 1) * NX + i) * NX, 1, s.v);
           const float *Br = V.gB + ((int64_t)(k - 1) * NX + i) * nu;
-          for (int j = 0; j < nu; ++j) acc = rfma((Real)__ldg(Br + j), vu[j], acc);
+          for (int j = 0; j < nu; ++j) ab = rfma((Real)__ldg(Br + j), vu[j], ab);
         }
+        acc += ab;
       }
       return acc;
     } else {
@@ -302,9 +310,8 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     }
   };
   auto apply_P_row = [&](const Real *src, int k, int i) -> Real {
-    if (k < K) return bt_row<NX, true, Real>(V.sPD, V.sPE, V.ld, N, k, i, src);
-    if (V.gPEt) return bt_row_t<NX, Real>(V.gPD, V.gPE, V.gPEt, N, k, i, src);
-    return bt_row<NX, false, Real>(V.gPD, V.gPE, NX, N, k, i, src);
+    return k < K ? bt_row<NX, true, Real>(V.sPD, V.sPE, V.ld, N, k, i, src)
+                 : bt_row<NX, false, Real>(V.gPD, V.gPE, NX, N, k, i, src);
   };
 
   __syncthreads();  // staged blocks and reciprocals visible
@@ -312,11 +319,13 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   // ---- r0 = gamma - S x0, z0 = Phi^-1 r0, p0 = z0 ----
   AccT g1[1] = {R::zero()};
   for (int row = tid; row < R_; row += T) {
+    int k, i;
+    const int si = vid(row, k, i);
     const Real g = (Real)gam[row];
     g1[0] = R::fma(g1[0], g, g);
     const Real x0 = a.warm ? lam_load(row) : Real(0);
-    sp[row] = x0;
-    sx[row] = x0;
+    sp[si] = x0;
+    sx[si] = x0;
   }
   block_sum<R, 1>(g1, slots);  // contains a barrier: sp complete
   const Real gg = R::get(g1[0]);
@@ -332,11 +341,15 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   if (warm) {
     apply_S_phase1(sp);
     for (int row = tid; row < R_; row += T) {
-      const int k = row / NX, i = row - k * NX;
-      sr[row] = (Real)gam[row] - apply_S_row(sp, k, i);
+      int k, i;
+      const int si = vid(row, k, i);
+      sr[si] = (Real)gam[row] - apply_S_row(sp, k, i);
     }
   } else {
-    for (int row = tid; row < R_; row += T) sr[row] = (Real)gam[row];
+    for (int row = tid; row < R_; row += T) {
+      int k, i;
+      sr[vid(row, k, i)] = (Real)gam[row];
+    }
   }
   __syncthreads();
   AccT s2[2];
@@ -344,10 +357,11 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   for (int pass = 0; pass < 2; ++pass) {
     s2[0] = R::zero(); s2[1] = R::zero();
     for (int row = tid; row < R_; row += T) {
-      const int k = row / NX, i = row - k * NX;
+      int k, i;
+      const int si = vid(row, k, i);
       const Real z = apply_P_row(sr, k, i);
-      const Real r = sr[row];
-      sw[row] = z;
+      const Real r = sr[si];
+      sw[si] = z;
       s2[0] = R::fma(s2[0], r, z);
       s2[1] = R::fma(s2[1], r, r);
     }
@@ -356,14 +370,23 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     rr = R::get(s2[1]);
     // warm start with fallback: restart from zero if lambda_0 is no better than zero
     if (pass == 0 && warm && a.warm == 2 && !(rr < gg)) {
-      for (int row = tid; row < R_; row += T) { sr[row] = (Real)gam[row]; sx[row] = Real(0); }
+      for (int row = tid; row < R_; row += T) {
+        int k, i;
+        const int si = vid(row, k, i);
+        sr[si] = (Real)gam[row];
+        sx[si] = Real(0);
+      }
       warm = false;
       __syncthreads();
       continue;
     }
     break;
   }
-  for (int row = tid; row < R_; row += T) sp[row] = sw[row];
+  for (int row = tid; row < R_; row += T) {
+    int k, i;
+    const int si = vid(row, k, i);
+    sp[si] = sw[si];
+  }
   __syncthreads();
 
   // ---- iterations ----
@@ -378,27 +401,31 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     apply_S_phase1(sp);
     AccT s1[1] = {R::zero()};
     for (int row = tid; row < R_; row += T) {
-      const int k = row / NX, i = row - k * NX;
+      int k, i;
+      const int si = vid(row, k, i);
       const Real w = apply_S_row(sp, k, i);
-      sw[row] = w;
-      s1[0] = R::fma(s1[0], sp[row], w);
+      sw[si] = w;
+      s1[0] = R::fma(s1[0], sp[si], w);
     }
     block_sum<R, 1>(s1, slots);
     const Real pw = R::get(s1[0]);
     if (!(pw > Real(0)) || !isfinite(pw)) { code = isfinite(pw) ? kBreakdown : kNonFinite; break; }
     const Real alpha = rz / pw;
     for (int row = tid; row < R_; row += T) {
-      sx[row] = rfma(alpha, sp[row], sx[row]);
-      sr[row] = rfma(-alpha, sw[row], sr[row]);
+      int k, i;
+      const int si = vid(row, k, i);
+      sx[si] = rfma(alpha, sp[si], sx[si]);
+      sr[si] = rfma(-alpha, sw[si], sr[si]);
     }
     __syncthreads();
     // z = Phi^-1 r, r.z, r.r
     s2[0] = R::zero(); s2[1] = R::zero();
     for (int row = tid; row < R_; row += T) {
-      const int k = row / NX, i = row - k * NX;
+      int k, i;
+      const int si = vid(row, k, i);
       const Real z = apply_P_row(sr, k, i);
-      const Real r = sr[row];
-      sw[row] = z;
+      const Real r = sr[si];
+      sw[si] = z;
       s2[0] = R::fma(s2[0], r, z);
       s2[1] = R::fma(s2[1], r, r);
     }
@@ -407,11 +434,18 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     rr = R::get(s2[1]);
     const Real beta = rz_new / rz;
     rz = rz_new;
-    for (int row = tid; row < R_; row += T) sp[row] = rfma(beta, sp[row], sw[row]);
+    for (int row = tid; row < R_; row += T) {
+      int k, i;
+      const int si = vid(row, k, i);
+      sp[si] = rfma(beta, sp[si], sw[si]);
+    }
     __syncthreads();
     ++it;
   }
-  for (int row = tid; row < R_; row += T) lam_store(row, sx[row]);
+  for (int row = tid; row < R_; row += T) {
+    int k, i;
+    lam_store(row, sx[vid(row, k, i)]);
+  }
   if (tid == 0) {
     a.iters[p] = it;
     a.relres[p] = sqrt((double)rr / (double)gg);
