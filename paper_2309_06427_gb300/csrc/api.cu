@@ -80,22 +80,16 @@ int auto_block(int64_t rows) {
 
 // Staged block rows K and dynamic shared memory (bytes) of a PCG problem
 // under a schedule; false when even the vectors do not fit.
-// *nwarps: on entry the warps of the launch, on return possibly fewer, so
-// that the per-warp staging buffers of streamed rows fit beside the vectors.
-bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int *K, int64_t *bytes, int *nwarps) {
+// nwarps: warps of the launch (the staging buffers of streamed rows are per warp).
+bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int *K, int64_t *bytes, int nwarps = 16) {
   const int64_t esz = f64 ? sizeof(double) : sizeof(float);
   const int64_t budget = smem_budget() / esz;
-  for (int nw = *nwarps; nw >= 1; nw /= 2) {
-    int k = pcg_max_resident(op, N, nx, nu, budget, nw);
-    if (k < 0) continue;
-    if (sched == SSPCG_SCHED_STREAM) k = 0;
-    if (pcg_layout(op, k, N, nx, nu, nw).total > budget) continue;
-    *K = k;
-    *nwarps = nw;
-    *bytes = pcg_layout(op, k, N, nx, nu, nw).total * esz;
-    return true;
-  }
-  return false;
+  int k = pcg_max_resident(op, N, nx, nu, budget, nwarps);
+  if (k < 0) return false;
+  if (sched == SSPCG_SCHED_STREAM) k = 0;
+  *K = k;
+  *bytes = pcg_layout(op, k, N, nx, nu, nwarps).total * esz;
+  return true;
 }
 
 sspcg_status validate_opts(const sspcg_options *o) {
@@ -227,14 +221,11 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
   constexpr int kClasses = 5;
   std::vector<std::vector<int32_t>> buckets(kClasses * (kMaxNx + 1));
   std::vector<int64_t> bytes(descs.size(), 0);
-  std::vector<int> warps(descs.size(), 16);
   const int64_t budget = smem_budget();
   for (int32_t i : members) {
     const ProbDesc &d = descs[i];
     int K = 0;
-    if (p->opts.block_threads > 0) warps[i] = p->opts.block_threads / 32;
-    if (!pcg_fit(set.op, p->opts.schedule, d.N, d.nx, d.nu, set.f64, &K, &bytes[i], &warps[i]))
-      return SSPCG_ERR_UNSUPPORTED;
+    if (!pcg_fit(set.op, p->opts.schedule, d.N, d.nx, d.nu, set.f64, &K, &bytes[i])) return SSPCG_ERR_UNSUPPORTED;
     int cls = 0;
     if (K == d.N + 1) {
       const int64_t need = bytes[i] + kPcgStaticSmem + 1024;
@@ -252,15 +243,12 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
       g.resident = r != 0;
       g.f64 = set.f64;
       int64_t maxrows = 0, maxsmem = 0;
-      int minwarps = 16;
       for (int32_t i : b) {
         const ProbDesc &d = descs[i];
         maxrows = std::max<int64_t>(maxrows, (int64_t)(d.N + 1) * d.nx);
         maxsmem = std::max<int64_t>(maxsmem, bytes[i]);
-        minwarps = std::min(minwarps, warps[i]);
       }
       g.block = p->opts.block_threads > 0 ? p->opts.block_threads : auto_block(maxrows);
-      g.block = std::min(g.block, 32 * minwarps);
       g.smem = (size_t)maxsmem;
       const int64_t per_sm_smem = 228 * 1024;
       const int by_smem = (int)std::max<int64_t>(1, per_sm_smem / (maxsmem + kPcgStaticSmem + 1024));
@@ -433,9 +421,8 @@ static sspcg_status solve_single(int op, bool f64, int32_t N, int32_t nx, int32_
   if (op == kOpBlock && (!D || (N > 0 && !E))) return SSPCG_ERR_INVALID_ARG;
   int K = 0;
   int64_t bytes = 0;
-  int nw = (opts->block_threads > 0 ? opts->block_threads : auto_block((int64_t)(N + 1) * nx)) / 32;
-  if (!pcg_fit(op, opts->schedule, N, nx, nu, f64, &K, &bytes, &nw)) return SSPCG_ERR_UNSUPPORTED;
-  const int block = 32 * nw;
+  const int block = opts->block_threads > 0 ? opts->block_threads : auto_block((int64_t)(N + 1) * nx);
+  if (!pcg_fit(op, opts->schedule, N, nx, nu, f64, &K, &bytes, block / 32)) return SSPCG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   PcgArgs a = make_args(opts);
   a.ps = ProbSet{nullptr, single_desc(N, nx, nu), 1};

@@ -175,13 +175,9 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   const int p = d.id;  // output slot
   const int N = d.N, n = N + 1, nu = d.nu, R_ = n * NX, NUP = vec_stride(nu);
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
-  int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems, nwarps);
-  if (K < 0) {  // the host sizes every launch so that this cannot happen; never touch smem out of bounds
-    if (tid == 0) { a.iters[d.id] = -1; a.relres[d.id] = 0.0; a.status[d.id] = kNonFinite; }
-    __syncthreads();
-    return;
-  }
+  int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems, nwarps);  // the host sized smem so that K >= 0
   if (K > a.max_resident) K = a.max_resident;
+  if (K < 0) K = 0;
   const int Ks = K < N ? K : N;
   const PcgLayout L = pcg_layout(OP, K, N, NX, nu, nwarps);
   Real *stage = sm + L.st + warp * L.st_warp;  // this warp's staging buffer (streamed rows)
