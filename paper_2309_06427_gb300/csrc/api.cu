@@ -80,15 +80,14 @@ int auto_block(int64_t rows) {
 
 // Staged block rows K and dynamic shared memory (bytes) of a PCG problem
 // under a schedule; false when even the vectors do not fit.
-// nwarps: warps of the launch (the staging buffers of streamed rows are per warp).
-bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int *K, int64_t *bytes, int nwarps = 16) {
+bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int *K, int64_t *bytes) {
   const int64_t esz = f64 ? sizeof(double) : sizeof(float);
   const int64_t budget = smem_budget() / esz;
-  int k = pcg_max_resident(op, N, nx, nu, budget, nwarps);
+  int k = pcg_max_resident(op, N, nx, nu, budget);
   if (k < 0) return false;
   if (sched == SSPCG_SCHED_STREAM) k = 0;
   *K = k;
-  *bytes = pcg_layout(op, k, N, nx, nu, nwarps).total * esz;
+  *bytes = pcg_layout(op, k, N, nx, nu).total * esz;
   return true;
 }
 
@@ -421,8 +420,7 @@ static sspcg_status solve_single(int op, bool f64, int32_t N, int32_t nx, int32_
   if (op == kOpBlock && (!D || (N > 0 && !E))) return SSPCG_ERR_INVALID_ARG;
   int K = 0;
   int64_t bytes = 0;
-  const int block = opts->block_threads > 0 ? opts->block_threads : auto_block((int64_t)(N + 1) * nx);
-  if (!pcg_fit(op, opts->schedule, N, nx, nu, f64, &K, &bytes, block / 32)) return SSPCG_ERR_UNSUPPORTED;
+  if (!pcg_fit(op, opts->schedule, N, nx, nu, f64, &K, &bytes)) return SSPCG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   PcgArgs a = make_args(opts);
   a.ps = ProbSet{nullptr, single_desc(N, nx, nu), 1};
@@ -430,6 +428,7 @@ static sspcg_status solve_single(int op, bool f64, int32_t N, int32_t nx, int32_
   a.A = A; a.B = B; a.qd = qd; a.rd = rd; a.D = D; a.E = E; a.PD = PD; a.PE = PE;
   a.gamma = gamma; a.lambda = lambda; a.iters = iters; a.relres = relres; a.status = status;
   a.lambda_f32 = f64 ? 0 : 1;
+  const int block = opts->block_threads > 0 ? opts->block_threads : auto_block((int64_t)(N + 1) * nx);
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
   SSPCG_CUDA(launch_pcg(nx, op, f64 ? kRedF64 : red_mode(opts->reduction), f64, a, 1, block, (size_t)bytes, st));
   return SSPCG_OK;

@@ -26,20 +26,15 @@ struct PcgLayout {
   int64_t p, r, w, x, v;            // vectors
   int64_t iq, ir;                   // 1/q, 1/r (QP form)
   int64_t m0, m1, pd, pe;           // staged blocks
-  int64_t st, st_warp;              // per-warp staging buffers of the streamed rows (K < N+1)
   int64_t total;
 };
-
-// Block rows a warp takes at a time in the streamed part: lane g*nx + i
-// handles row i of the g-th one.
-__host__ __device__ __forceinline__ int rows_per_warp(int nx) { return nx <= 32 ? 32 / nx : 1; }
 
 // Vectors are stored with a block-row stride of nx rounded up to 4 elements,
 // so that every block row starts 16-byte aligned and a thread can load a
 // whole block-row segment with 128-bit loads.
 __host__ __device__ __forceinline__ int vec_stride(int x) { return (x + 3) & ~3; }
 
-__host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, int nu, int nwarps) {
+__host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, int nu) {
   PcgLayout L{};
   const int64_t n = N + 1, NXP = vec_stride(nx), NUP = vec_stride(nu), RV = n * NXP;
   const int64_t Ks = K < N ? K : N;  // staged off-diagonal slots
@@ -64,28 +59,19 @@ __host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, in
   }
   L.pd = o; o += round_up((int64_t)K * nx * ld, 4);    // PD_k
   L.pe = o; o += round_up(Ks * nx * ld, 4);            // PE_k
-  // streamed rows stage their row-accessed blocks (A_{k-1} and B_{k-1}, or the
-  // sub-diagonal preconditioner block) per warp
-  L.st = o;
-  L.st_warp = 0;
-  if (K < n) {
-    const int64_t G = rows_per_warp(nx);
-    L.st_warp = round_up(G * nx * (ld + (op == kOpQp ? ldb : 0)), 4);
-    o += nwarps * L.st_warp;
-  }
   L.total = o;
   return L;
 }
 
 // Largest number of staged block rows whose layout fits in ``elems``; -1 when
 // not even the vectors fit.
-__host__ __device__ inline int pcg_max_resident(int op, int N, int nx, int nu, int64_t elems, int nwarps) {
-  if (pcg_layout(op, N + 1, N, nx, nu, nwarps).total <= elems) return N + 1;
-  if (pcg_layout(op, 0, N, nx, nu, nwarps).total > elems) return -1;
+__host__ __device__ inline int pcg_max_resident(int op, int N, int nx, int nu, int64_t elems) {
+  if (pcg_layout(op, N + 1, N, nx, nu).total <= elems) return N + 1;
+  if (pcg_layout(op, 0, N, nx, nu).total > elems) return -1;
   int lo = 0, hi = N;  // invariant: layout(lo) fits, layout(hi + 1) does not
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
-    if (pcg_layout(op, mid, N, nx, nu, nwarps).total <= elems) lo = mid; else hi = mid - 1;
+    if (pcg_layout(op, mid, N, nx, nu).total <= elems) lo = mid; else hi = mid - 1;
   }
   return lo;
 }

@@ -174,13 +174,12 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   constexpr int NXP = (NX + 3) & ~3;
   const int p = d.id;  // output slot
   const int N = d.N, n = N + 1, nu = d.nu, R_ = n * NX, NUP = vec_stride(nu);
-  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
-  int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems, nwarps);  // the host sized smem so that K >= 0
+  const int tid = threadIdx.x, T = blockDim.x;
+  int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems);  // the host sized smem so that K >= 0
   if (K > a.max_resident) K = a.max_resident;
   if (K < 0) K = 0;
   const int Ks = K < N ? K : N;
-  const PcgLayout L = pcg_layout(OP, K, N, NX, nu, nwarps);
-  Real *stage = sm + L.st + warp * L.st_warp;  // this warp's staging buffer (streamed rows)
+  const PcgLayout L = pcg_layout(OP, K, N, NX, nu);
   Real *sp = sm + L.p, *sr = sm + L.r, *sw = sm + L.w, *sx = sm + L.x, *sv = sm + L.v;
   Real *svu = sv + n * NXP;  // v_u block rows, stride NUP
   const float *gam = a.gamma + d.ovec;
@@ -283,127 +282,36 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       __syncthreads();
     }
   };
-  // Resident row (k < K), QP form: w_k[i] = -v_x(k)[i] + A_{k-1}[i,:] v_x(k-1) + B_{k-1}[i,:] v_u(k-1).
-  auto S_row_res = [&](const Real *src, int k, int i) -> Real {
+  // Row (k, i) of S src (QP form: of C sv).
+  //   w_k[i] = -v_x(k)[i] + A_{k-1}[i,:] v_x(k-1) + B_{k-1}[i,:] v_u(k-1)
+  auto apply_S_row = [&](const Real *src, int k, int i) -> Real {
     if constexpr (OP == kOpQp) {
       Real acc = -sv[k * NXP + i];
       if (k > 0) {
         Seg<NX, Real> s;
         s.load(sv + (k - 1) * NXP);
-        acc += dot_seg<NX, true, Real>(V.sA + ((k - 1) * NX + i) * V.ld, 1, s.v);
-        const Real *Br = V.sB + ((k - 1) * NX + i) * V.ldb;
         const Real *vu = svu + (k - 1) * NUP;
         Real ab = Real(0);
-        for (int j = 0; j < nu; ++j) ab = rfma(Br[j], vu[j], ab);
+        if (k < K) {
+          acc += dot_seg<NX, true, Real>(V.sA + ((k - 1) * NX + i) * V.ld, 1, s.v);
+          const Real *Br = V.sB + ((k - 1) * NX + i) * V.ldb;
+          for (int j = 0; j < nu; ++j) ab = rfma(Br[j], vu[j], ab);
+        } else {
+          acc += dot_seg<NX, false, Real>(V.gA + ((int64_t)(k - 1) * NX + i) * NX, 1, s.v);
+          const float *Br = V.gB + ((int64_t)(k - 1) * NX + i) * nu;
+          for (int j = 0; j < nu; ++j) ab = rfma((Real)__ldg(Br + j), vu[j], ab);
+        }
         acc += ab;
       }
       return acc;
     } else {
-      return bt_row<NX, true, Real>(V.sD, V.sE, V.ld, N, k, i, src);
+      return k < K ? bt_row<NX, true, Real>(V.sD, V.sE, V.ld, N, k, i, src)
+                   : bt_row<NX, false, Real>(V.gD, V.gE, NX, N, k, i, src);
     }
   };
-  auto P_row_res = [&](const Real *src, int k, int i) -> Real {
-    return bt_row<NX, true, Real>(V.sPD, V.sPE, V.ld, N, k, i, src);
-  };
-
-  // Streamed rows (k >= K): each warp takes G consecutive block rows at a time
-  // (lane g*NX + i: row i of block row k0 + g).  The blocks read by rows --
-  // A_{k-1} and B_{k-1} for S (QP form), the sub-diagonal block for
-  // Phi^-1 (and for S in block form) -- are first copied by the whole warp,
-  // coalesced, into the warp's staging buffer (odd row strides); the blocks
-  // read by columns come straight from global memory, coalesced.
-  constexpr int G = (NX <= 32) ? 32 / NX : 1;
-  const int sg = lane / NX, si_ = lane - sg * NX;  // this lane's block-row slot and row
-  auto stage_blocks_warp = [&](Real *dst, int ldd, const auto *src, int cols, int k0) {
-    // dst[(g*NX + r)*ldd + c] = src block (k0 + g - 1) [r][c], for the G block rows of the group
-    for (int e = lane; e < G * NX * cols; e += 32) {
-      const int g = e / (NX * cols), rem = e - g * NX * cols, r = rem / cols, c = rem - r * cols;
-      const int kk = k0 + g;
-      if (kk >= 1 && kk <= N) dst[(g * NX + r) * ldd + c] = (Real)__ldg(src + (int64_t)(kk - 1) * NX * cols + rem);
-    }
-  };
-  auto for_streamed = [&](auto &&stage_fn, auto &&row_fn) {
-    for (int k0 = K + warp * G; k0 < n; k0 += nwarps * G) {
-      stage_fn(k0);
-      __syncwarp();
-      const int k = k0 + sg;
-      if (sg < G && k < n) row_fn(k, si_, sg);
-      __syncwarp();
-    }
-  };
-
-  // All rows of S src: emit(si, value) for every row this thread owns.
-  auto for_S_rows = [&](const Real *src, auto &&emit) {
-    for (int row = tid; row < K * NX; row += T) {
-      int k, i;
-      const int si = vid(row, k, i);
-      emit(si, S_row_res(src, k, i));
-    }
-    if (K < n) {
-      if constexpr (OP == kOpQp) {
-        Real *stA = stage, *stB = stage + G * NX * V.ld;
-        for_streamed(
-            [&](int k0) {
-              stage_blocks_warp(stA, V.ld, V.gA, NX, k0);
-              if (nu > 0) stage_blocks_warp(stB, V.ldb, V.gB, nu, k0);
-            },
-            [&](int k, int i, int g) {
-              Real acc = -sv[k * NXP + i];
-              if (k > 0) {
-                Seg<NX, Real> s;
-                s.load(sv + (k - 1) * NXP);
-                acc += dot_seg<NX, true, Real>(stA + (g * NX + i) * V.ld, 1, s.v);
-                const Real *Br = stB + (g * NX + i) * V.ldb;
-                const Real *vu = svu + (k - 1) * NUP;
-                Real ab = Real(0);
-                for (int j = 0; j < nu; ++j) ab = rfma(Br[j], vu[j], ab);
-                acc += ab;
-              }
-              emit(k * NXP + i, acc);
-            });
-      } else {
-        for_streamed([&](int k0) { stage_blocks_warp(stage, V.ld, V.gE, NX, k0); },
-                     [&](int k, int i, int g) {
-                       Seg<NX, Real> s;
-                       s.load(src + k * NXP);
-                       Real acc = dot_seg<NX, false, Real>(V.gD + (int64_t)k * NX * NX + i, NX, s.v);
-                       if (k > 0) {
-                         s.load(src + (k - 1) * NXP);
-                         acc += dot_seg<NX, true, Real>(stage + (g * NX + i) * V.ld, 1, s.v);
-                       }
-                       if (k < N) {
-                         s.load(src + (k + 1) * NXP);
-                         acc += dot_seg<NX, false, Real>(V.gE + (int64_t)k * NX * NX + i, NX, s.v);
-                       }
-                       emit(k * NXP + i, acc);
-                     });
-      }
-    }
-  };
-  // All rows of Phi^-1 src.
-  auto for_P_rows = [&](const Real *src, auto &&emit) {
-    for (int row = tid; row < K * NX; row += T) {
-      int k, i;
-      const int si = vid(row, k, i);
-      emit(si, P_row_res(src, k, i));
-    }
-    if (K < n) {
-      for_streamed([&](int k0) { stage_blocks_warp(stage, V.ld, V.gPE, NX, k0); },
-                   [&](int k, int i, int g) {
-                     Seg<NX, Real> s;
-                     s.load(src + k * NXP);
-                     Real acc = dot_seg<NX, false, Real>(V.gPD + (int64_t)k * NX * NX + i, NX, s.v);
-                     if (k > 0) {
-                       s.load(src + (k - 1) * NXP);
-                       acc += dot_seg<NX, true, Real>(stage + (g * NX + i) * V.ld, 1, s.v);
-                     }
-                     if (k < N) {
-                       s.load(src + (k + 1) * NXP);
-                       acc += dot_seg<NX, false, Real>(V.gPE + (int64_t)k * NX * NX + i, NX, s.v);
-                     }
-                     emit(k * NXP + i, acc);
-                   });
-    }
+  auto apply_P_row = [&](const Real *src, int k, int i) -> Real {
+    return k < K ? bt_row<NX, true, Real>(V.sPD, V.sPE, V.ld, N, k, i, src)
+                 : bt_row<NX, false, Real>(V.gPD, V.gPE, NX, N, k, i, src);
   };
 
   __syncthreads();  // staged blocks and reciprocals visible
@@ -432,12 +340,10 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   bool warm = a.warm != 0;
   if (warm) {
     apply_S_phase1(sp);
-    for_S_rows(sp, [&](int si, Real w) { sw[si] = w; });
-    __syncthreads();
     for (int row = tid; row < R_; row += T) {
       int k, i;
       const int si = vid(row, k, i);
-      sr[si] = (Real)gam[row] - sw[si];
+      sr[si] = (Real)gam[row] - apply_S_row(sp, k, i);
     }
   } else {
     for (int row = tid; row < R_; row += T) {
@@ -450,12 +356,15 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   Real rz, rr;
   for (int pass = 0; pass < 2; ++pass) {
     s2[0] = R::zero(); s2[1] = R::zero();
-    for_P_rows(sr, [&](int si, Real z) {
+    for (int row = tid; row < R_; row += T) {
+      int k, i;
+      const int si = vid(row, k, i);
+      const Real z = apply_P_row(sr, k, i);
       const Real r = sr[si];
       sw[si] = z;
       s2[0] = R::fma(s2[0], r, z);
       s2[1] = R::fma(s2[1], r, r);
-    });
+    }
     block_sum<R, 2>(s2, slots + 64);
     rz = R::get(s2[0]);
     rr = R::get(s2[1]);
@@ -491,10 +400,13 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     // w = S p, p.w
     apply_S_phase1(sp);
     AccT s1[1] = {R::zero()};
-    for_S_rows(sp, [&](int si, Real w) {
+    for (int row = tid; row < R_; row += T) {
+      int k, i;
+      const int si = vid(row, k, i);
+      const Real w = apply_S_row(sp, k, i);
       sw[si] = w;
       s1[0] = R::fma(s1[0], sp[si], w);
-    });
+    }
     block_sum<R, 1>(s1, slots);
     const Real pw = R::get(s1[0]);
     if (!(pw > Real(0)) || !isfinite(pw)) { code = isfinite(pw) ? kBreakdown : kNonFinite; break; }
@@ -508,12 +420,15 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     __syncthreads();
     // z = Phi^-1 r, r.z, r.r
     s2[0] = R::zero(); s2[1] = R::zero();
-    for_P_rows(sr, [&](int si, Real z) {
+    for (int row = tid; row < R_; row += T) {
+      int k, i;
+      const int si = vid(row, k, i);
+      const Real z = apply_P_row(sr, k, i);
       const Real r = sr[si];
       sw[si] = z;
       s2[0] = R::fma(s2[0], r, z);
       s2[1] = R::fma(s2[1], r, r);
-    });
+    }
     block_sum<R, 2>(s2, slots + 64);
     const Real rz_new = R::get(s2[0]);
     rr = R::get(s2[1]);
