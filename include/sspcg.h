@@ -320,6 +320,44 @@ sspcg_status sspcg_pipeline_host(sspcg_plan *plan, sspcg_precond kind, const flo
                                  float *lambda_host, int32_t *iters_host, double *relres_host, int32_t *status_host,
                                  sspcg_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* Batched solve without allocation                                   */
+/* ------------------------------------------------------------------ */
+
+/* Largest batch of sspcg_solve_qp_batched_noalloc. */
+#define SSPCG_NOALLOC_MAX_PROBLEMS 4096
+
+/*
+ * sspcg_solve_qp_batched without a plan and without allocating anything,
+ * for callers that cannot call cudaMalloc once running: a model-predictive
+ * control loop on a real-time thread (cudaMalloc may synchronise the device
+ * and take unbounded time), or an application whose own allocator owns all
+ * device memory.  The paper has no counterpart; this is a library service.
+ *
+ * N, nx, nu: HOST arrays of nprob <= SSPCG_NOALLOC_MAX_PROBLEMS entries;
+ * more return SSPCG_ERR_INVALID_ARG.  The device arrays are packed as by a
+ * plan (sspcg_plan_offsets): problem i of each array kind starts at the
+ * prefix sum of the sizes of problems 0..i-1, each size rounded up to a
+ * multiple of 4 elements.  Other arguments as in sspcg_solve_qp_batched
+ * (FP32, factored S).
+ *
+ * Scratch: problem descriptors, the work list and work-queue counters live
+ * in one file-scope __device__ array of 311,552 bytes (4096 descriptors),
+ * which every GPU that loads the library holds until the process exits.
+ * Each call copies its descriptors there with cudaMemcpyAsync from host
+ * memory and clears the counters on ``stream``; all calls share the array,
+ * so calls that overlap on the GPU (on different streams without ordering)
+ * race and give wrong results.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  No cudaMalloc, cudaFree or allocating library routine
+ * is called.
+ */
+sspcg_status sspcg_solve_qp_batched_noalloc(int32_t nprob, const int32_t *N, const int32_t *nx, const int32_t *nu,
+                                            const float *A, const float *B, const float *qd, const float *rd,
+                                            const float *PD, const float *PE, const float *gamma, float *lambda,
+                                            const sspcg_options *opts, int32_t *iters, double *relres,
+                                            int32_t *status, sspcg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,19 @@ sspcg_status validate_opts(const sspcg_options *o) {
 namespace sspcg {
 // Largest dynamic shared memory of a PCG launch (opt-in limit minus the static part).
 int pcg_max_smem_bytes() { return max_smem_optin() - kPcgStaticSmem; }
+
+// Host helpers shared with the other entry-point units.
+namespace host {
+int sms() { return device_sms(); }
+int reduction_mode(int32_t r) { return red_mode(r); }
+int block_for_rows(int64_t rows) { return auto_block(rows); }
+bool fit(int op, int sched, int N, int nx, int nu, bool f64, int *K, int64_t *bytes) {
+  return pcg_fit(op, sched, N, nx, nu, f64, K, bytes);
+}
+sspcg_status check_options(const sspcg_options *o) { return validate_opts(o); }
+bool valid_shape(int N, int nx, int nu) { return shape_ok(N, nx, nu); }
+sspcg_status cuda_error(cudaError_t e) { return cuda_fail(e); }
+}  // namespace host
 }  // namespace sspcg
 
 // ---------------------------------------------------------------------------

@@ -26,6 +26,7 @@ PRECISION = {"auto": 0, "f32": 1, "f64": 2}
 ARRAY_A, ARRAY_B, ARRAY_QD, ARRAY_RD, ARRAY_DIAG, ARRAY_OFF, ARRAY_VEC = range(7)
 NUM_ARRAYS = 7
 MAX_NX = 28
+NOALLOC_MAX_PROBLEMS = 4096
 
 
 class SspcgError(RuntimeError):
@@ -83,6 +84,7 @@ def lib() -> ctypes.CDLL:
             "sspcg_residual_qp_batched": [_VP] * 9,
             "sspcg_pipeline_batched": [_VP, _I32] + [_VP] * 14,
             "sspcg_pipeline_host": [_VP, _I32] + [_VP] * 10,
+            "sspcg_solve_qp_batched_noalloc": [_I32] + [_VP] * 11 + [ctypes.POINTER(Options)] + [_VP] * 4,
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -308,6 +310,18 @@ def sspcg_pipeline_host(plan: Plan, kind, A, B, qd, rd, gamma, lam, iters, relre
     hp = lambda t: t.data_ptr() if t is not None else None
     _check(lib().sspcg_pipeline_host(plan.handle, k, hp(A), hp(B), hp(qd), hp(rd), hp(gamma), hp(lam), hp(iters),
                                      hp(relres), hp(status), _stream(stream)), "sspcg_pipeline_host")
+
+
+def sspcg_solve_qp_batched_noalloc(N, nx, nu, A, B, qd, rd, PD, PE, gamma, lam, opts: Options, iters, relres, status,
+                                   stream=None):
+    """Batched FP32 solve without a plan and without any device allocation (shape arrays on the host)."""
+    N = np.ascontiguousarray(N, dtype=np.int32)
+    nx = np.ascontiguousarray(nx, dtype=np.int32)
+    nu = np.ascontiguousarray(nu, dtype=np.int32)
+    _check(lib().sspcg_solve_qp_batched_noalloc(len(N), N.ctypes.data, nx.ctypes.data, nu.ctypes.data, _ptr(A),
+                                                _ptr(B), _ptr(qd), _ptr(rd), _ptr(PD), _ptr(PE), _ptr(gamma),
+                                                _ptr(lam), ctypes.byref(opts), _ptr(iters), _ptr(relres),
+                                                _ptr(status), _stream(stream)), "sspcg_solve_qp_batched_noalloc")
 
 
 # ---------------------------------------------------------------------------
