@@ -197,3 +197,24 @@ def custom_problems(shapes: Iterable[Sequence[int]], h: float = 0.05, config: in
         nu = int(s[2]) if len(s) > 2 else nu_for(nx)
         out.append(make_problem(config_key(config, i), N, nx, nu, h))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Warm-start network: seeded initial weights (inputs, like the problems).
+# ---------------------------------------------------------------------------
+MLP_SHAPES = ((256, 1344), (256,), (256, 256), (256,), (32, 256), (32,))
+
+
+def mlp_initial_params(seed: int = 0) -> np.ndarray:
+    """Flat FP32 initial parameters [W1, b1, W2, b2, W3, b3] of the warm-start network.
+
+    W1 and W2 ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from stream ``2**62 + seed``
+    (W1 first, then W2); biases zero; the output layer W3, b3 zero, so that the
+    untrained network predicts lambda0 = 0 (the plain method's start)."""
+    key = (1 << 62) + seed
+    n1, n2 = 256 * 1344, 256 * 256
+    u = uniform01(key, n1 + n2, 0)
+    w1 = (2.0 * u[:n1] - 1.0) / math.sqrt(1344)
+    w2 = (2.0 * u[n1:] - 1.0) / math.sqrt(256)
+    parts = [w1, np.zeros(256), w2, np.zeros(256), np.zeros(32 * 256), np.zeros(32)]
+    return np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)
