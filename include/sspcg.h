@@ -358,6 +358,100 @@ sspcg_status sspcg_solve_qp_batched_noalloc(int32_t nprob, const int32_t *N, con
                                             const sspcg_options *opts, int32_t *iters, double *relres,
                                             int32_t *status, sspcg_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* Learned warm start                                                 */
+/* ------------------------------------------------------------------ */
+/*
+ * A 3-layer ReLU network maps the data of each knot to an initial guess
+ * lambda_0 for the PCG solve.  The paper has no learned component: this is
+ * the warm-start extension of the method (a plain start lambda_0 = 0 remains
+ * the fallback, sspcg_options.warm_start = 2).
+ *
+ * Knot features: row k of a problem (one per block row of S) holds, as FP32
+ * values normalised per column and rounded to bfloat16, in 1344 columns:
+ *   [0, 784)      A_{k-1} as [28][28] row-major (zero padded; zero for k = 0)
+ *   [784, 1176)   B_{k-1} as [28][14] row-major (zero padded; zero for k = 0)
+ *   [1176, 1204)  diag Q_{k-1}   [1204, 1218) diag R_{k-1}   (zero for k = 0)
+ *   [1218, 1246)  diag Q_k       [1246, 1274) gamma_k
+ *   [1274, 1302)  D_k^-1 gamma_k (from the preconditioner's diagonal blocks PD)
+ *   1302          nx / 28        [1303, 1344) zero
+ * These are the data from which block row k of S is built (Sec. II-A).
+ * Normalisation: x -> (x - mu) * inv_sigma per column.
+ *
+ * Network: H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Y = H2 W3^T + b3;
+ * lambda_0 of knot k = Y[k][0..nx).  Parameters are FP32 masters, flat in the
+ * order W1 [256][1344], b1 [256], W2 [256][256], b2 [256], W3 [32][256],
+ * b3 [32] (SSPCG_MLP_PARAMS floats); the products use bfloat16 copies of the
+ * weights and of X, H1, H2 and the output gradient, with FP32 accumulation.
+ *
+ * Training loss of a minibatch of P whole problems: the mean over problems
+ * of ||S (lambda_0 - lambda*)||^2 / ||gamma||^2, where lambda* is the plain
+ * method's solution.  Since S lambda* = gamma up to the solve tolerance this
+ * is the squared relative initial residual that the PCG exit test measures.
+ * Optimiser: Adam (Kingma & Ba 2015) on the FP32 masters.
+ *
+ * The problem tables (shapes, packed offsets) come from a plan; every array
+ * argument is a device pointer in the plan's packed layout.  A network object
+ * owns its parameters, Adam state and the workspace of max_rows knot rows.
+ */
+#define SSPCG_MLP_IN 1344
+#define SSPCG_MLP_HIDDEN 256
+#define SSPCG_MLP_OUT 32
+#define SSPCG_MLP_PARAMS 418336
+
+typedef struct sspcg_mlp sspcg_mlp;
+
+typedef struct {
+  float lr;    /* step size */
+  float beta1; /* first-moment decay */
+  float beta2; /* second-moment decay */
+  float eps;   /* denominator guard */
+} sspcg_adam;
+
+/* Create a network with workspace for max_rows >= 1 knot rows per call chunk.
+ * Parameters start at zero; normalisation at mu = 0, inv_sigma = 1. */
+sspcg_status sspcg_mlp_create(sspcg_mlp **mlp, int32_t max_rows);
+sspcg_status sspcg_mlp_destroy(sspcg_mlp *mlp);
+/* Copy SSPCG_MLP_PARAMS FP32 values from a device array into the network and reset the Adam state. */
+sspcg_status sspcg_mlp_set_params(sspcg_mlp *mlp, const float *params, sspcg_stream stream);
+/* Copy the FP32 parameters (or the gradients of the last training step) to a device array. */
+sspcg_status sspcg_mlp_get_params(const sspcg_mlp *mlp, float *params, sspcg_stream stream);
+sspcg_status sspcg_mlp_get_grads(const sspcg_mlp *mlp, float *grads, sspcg_stream stream);
+/* Per-column normalisation (device arrays of SSPCG_MLP_IN floats). */
+sspcg_status sspcg_mlp_set_normalisation(sspcg_mlp *mlp, const float *mu, const float *inv_sigma,
+                                         sspcg_stream stream);
+sspcg_status sspcg_mlp_get_normalisation(const sspcg_mlp *mlp, float *mu, float *inv_sigma, sspcg_stream stream);
+/* Fit the normalisation to every knot of the plan's batch: mu = column mean, inv_sigma = 1 / population
+ * standard deviation (FP64 sums); a column whose standard deviation is at most 1e-6 of its RMS is constant
+ * and gets inv_sigma = 0.  PD: diagonal preconditioner blocks D_k^-1 (any block preconditioner). */
+sspcg_status sspcg_mlp_fit_normalisation(sspcg_mlp *mlp, const sspcg_plan *plan, const float *A, const float *B,
+                                         const float *qd, const float *rd, const float *gamma, const float *PD,
+                                         sspcg_stream stream);
+/* Normalised bfloat16 feature rows of problems [p_begin, p_end) into X [rows][SSPCG_MLP_IN] (uint16 bit
+ * patterns), rows in problem order.  The rows must fit the network's max_rows. */
+sspcg_status sspcg_mlp_features(const sspcg_mlp *mlp, const sspcg_plan *plan, int32_t p_begin, int32_t p_end,
+                                const float *A, const float *B, const float *qd, const float *rd,
+                                const float *gamma, const float *PD, uint16_t *X, sspcg_stream stream);
+/* lambda_0 for every problem of the plan, written into lambda0 (vector layout). */
+sspcg_status sspcg_mlp_infer(sspcg_mlp *mlp, const sspcg_plan *plan, const float *A, const float *B,
+                             const float *qd, const float *rd, const float *gamma, const float *PD, float *lambda0,
+                             sspcg_stream stream);
+/* One training step on problems [p_begin, p_end) (whole problems; their rows must fit max_rows): forward,
+ * loss, backward and one Adam step.  D, E: FP32 Schur blocks (sspcg_build_schur_batched); PD: D_k^-1 blocks;
+ * lambda_star: the plain method's solutions (vector layout).  loss: device FP64 scalar (the minibatch loss
+ * before the update). */
+sspcg_status sspcg_mlp_train_step(sspcg_mlp *mlp, const sspcg_plan *plan, int32_t p_begin, int32_t p_end,
+                                  const float *A, const float *B, const float *qd, const float *rd,
+                                  const float *gamma, const float *D, const float *E, const float *PD,
+                                  const float *lambda_star, const sspcg_adam *hyper, double *loss,
+                                  sspcg_stream stream);
+/* sspcg_pipeline_batched started from the network's lambda_0: blocks and preconditioner, inference into
+ * lambda, then PCG with warm start and fallback to lambda_0 = 0 (warm_start = 2) for every problem. */
+sspcg_status sspcg_pipeline_warm_batched(sspcg_plan *plan, sspcg_mlp *mlp, sspcg_precond kind, const float *A,
+                                         const float *B, const float *qd, const float *rd, const float *gamma,
+                                         float *D, float *E, float *PD, float *PE, float *lambda, int32_t *iters,
+                                         double *relres, int32_t *status, sspcg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

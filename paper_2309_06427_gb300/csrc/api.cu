@@ -8,6 +8,7 @@
 
 #include "../../include/sspcg.h"
 #include "common.cuh"
+#include "host.h"
 #include "kernels.h"
 
 using namespace sspcg;
@@ -175,6 +176,8 @@ struct sspcg_plan {
   ProbDesc *d_desc = nullptr;
   int2 *d_kref = nullptr, *d_oref = nullptr;  // (problem, block row) per knot / off-diagonal block
   int64_t total_knots = 0, total_off = 0;
+  std::vector<int64_t> knot_start;      // first knot (index into d_kref) of each problem, nprob + 1 entries
+  int64_t *d_knot_start = nullptr;
   // FP64 subset: descriptors whose odiag/ooff point into plan-owned FP64 blocks
   int32_t ntiny = 0;
   std::vector<ProbDesc> tdesc;
@@ -207,7 +210,7 @@ namespace {
 void plan_free(sspcg_plan *p) {
   if (!p) return;
   if (p->graph) cudaGraphExecDestroy(p->graph);
-  for (void *ptr : {(void *)p->d_desc, (void *)p->d_kref, (void *)p->d_oref, (void *)p->d_tdesc,
+  for (void *ptr : {(void *)p->d_desc, (void *)p->d_kref, (void *)p->d_oref, (void *)p->d_knot_start, (void *)p->d_tdesc,
                     (void *)p->d_tkref, (void *)p->d_toref, (void *)p->D64, (void *)p->E64,
                     (void *)p->PD64, (void *)p->PE64, (void *)p->d_work, (void *)p->d_counters, (void *)p->hbuf,
                     (void *)p->hint, (void *)p->hdbl})
@@ -525,6 +528,7 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
   for (int k = 0; k < SSPCG_NUM_ARRAYS; ++k) p->sizes[k] = cur[k];
   p->total_knots = knot_start[nprob];
   p->total_off = off_start[nprob];
+  p->knot_start = knot_start;
   // FP64 subset: same inputs, FP64 blocks in plan memory
   p->ntiny = (int32_t)tiny.size();
   std::vector<int64_t> tknot(p->ntiny + 1, 0), toff(p->ntiny + 1, 0);
@@ -548,6 +552,7 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     if ((e = upload(&p->d_desc, p->hdesc)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = upload(&p->d_kref, row_refs(p->hdesc, 0))) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = upload(&p->d_oref, row_refs(p->hdesc, 1))) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = upload(&p->d_knot_start, p->knot_start)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = make_nx_groups(p->hdesc, all, p->nxg_all)) != cudaSuccess) return fail(cuda_fail(e));
     if (p->ntiny > 0) {
       std::vector<int32_t> tl(p->ntiny);
@@ -745,19 +750,14 @@ sspcg_status sspcg_residual_qp_batched(sspcg_plan *plan, const float *A, const f
   return SSPCG_OK;
 }
 
-sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
-                                    const float *qd, const float *rd, const float *gamma, float *D, float *E,
-                                    float *PD, float *PE, float *lambda, int32_t *iters, double *relres,
-                                    int32_t *status, sspcg_stream stream) {
-  if (!plan || kind < 0 || kind > 3) return SSPCG_ERR_INVALID_ARG;
-  if (plan->nprob == 0) return SSPCG_OK;
-  sspcg_status s = check_solve_args(plan, kOpQp, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters,
-                                    relres, status);
-  if (s != SSPCG_OK) return s;
-  if (!D || (plan->total_off > 0 && !E)) return SSPCG_ERR_INVALID_ARG;
+// First half of the pipeline: FP32 blocks for every problem (also returned to the caller), FP64 blocks for
+// the FP64 subset.
+static sspcg_status pipeline_build(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
+                                   const float *qd, const float *rd, float *D, float *E, float *PD, float *PE,
+                                   int32_t *status, sspcg_stream stream) {
+  sspcg_status s;
   cudaStream_t st = (cudaStream_t)stream;
   time_mark(plan, 0, st);
-  // FP32 blocks for every problem (also returned to the caller), FP64 blocks for the FP64 subset
   if ((s = sspcg_build_schur_batched(plan, A, B, qd, rd, D, E, stream)) != SSPCG_OK) return s;
   if ((s = sspcg_build_precond_batched(plan, kind, D, E, PD, PE, status, stream)) != SSPCG_OK) return s;
   if (plan->ntiny > 0) {
@@ -770,16 +770,42 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
                                           plan->PD64, plan->PE64, st, device_sms(), plan->t_offe, plan->mx_tiny));
   }
   plan->build_timed = true;
+  return SSPCG_OK;
+}
+
+// Second half: the PCG launches of the FP32 set and the FP64 subset (``warm`` overrides the plan's
+// warm-start option).
+static sspcg_status pipeline_solve(sspcg_plan *plan, const float *A, const float *B, const float *qd,
+                                   const float *rd, const float *gamma, const float *PD, const float *PE,
+                                   float *lambda, int32_t *iters, double *relres, int32_t *status, int warm,
+                                   sspcg_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
   time_mark(plan, 1, st);
   PcgArgs a32 = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
+  a32.warm = warm;
   PcgArgs a64 = a32;
   a64.ps = tiny_set(plan);
   a64.PD = plan->PD64;
   a64.PE = plan->PE64;
 
-  s = launch_sets(plan, {{&plan->sets[kSetQpMain], a32}, {&plan->sets[kSetTiny], a64}}, st);
+  sspcg_status s = launch_sets(plan, {{&plan->sets[kSetQpMain], a32}, {&plan->sets[kSetTiny], a64}}, st);
   time_mark(plan, 2, st);
   return s;
+}
+
+sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
+                                    const float *qd, const float *rd, const float *gamma, float *D, float *E,
+                                    float *PD, float *PE, float *lambda, int32_t *iters, double *relres,
+                                    int32_t *status, sspcg_stream stream) {
+  if (!plan || kind < 0 || kind > 3) return SSPCG_ERR_INVALID_ARG;
+  if (plan->nprob == 0) return SSPCG_OK;
+  sspcg_status s = check_solve_args(plan, kOpQp, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters,
+                                    relres, status);
+  if (s != SSPCG_OK) return s;
+  if (!D || (plan->total_off > 0 && !E)) return SSPCG_ERR_INVALID_ARG;
+  if ((s = pipeline_build(plan, kind, A, B, qd, rd, D, E, PD, PE, status, stream)) != SSPCG_OK) return s;
+  return pipeline_solve(plan, A, B, qd, rd, gamma, PD, PE, lambda, iters, relres, status, plan->opts.warm_start,
+                        stream);
 }
 
 sspcg_status sspcg_plan_capture_pipeline(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
@@ -870,3 +896,32 @@ sspcg_status sspcg_pipeline_host(sspcg_plan *plan, sspcg_precond kind, const flo
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Host helpers for the warm-start unit (mlp_api.cu)
+// ---------------------------------------------------------------------------
+namespace sspcg {
+namespace host {
+PlanView plan_view(const sspcg_plan *p) {
+  PlanView v{};
+  v.nprob = p->nprob;
+  v.ps = ProbSet{p->d_desc, ProbDesc{}, p->nprob};
+  v.kref = p->d_kref;
+  v.knots = p->total_knots;
+  v.knot_start = p->knot_start.data();
+  v.d_knot_start = p->d_knot_start;
+  v.total_off = p->total_off;
+  return v;
+}
+sspcg_status build_half(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B, const float *qd,
+                        const float *rd, float *D, float *E, float *PD, float *PE, int32_t *status,
+                        sspcg_stream stream) {
+  return pipeline_build(plan, kind, A, B, qd, rd, D, E, PD, PE, status, stream);
+}
+sspcg_status solve_half(sspcg_plan *plan, const float *A, const float *B, const float *qd, const float *rd,
+                        const float *gamma, const float *PD, const float *PE, float *lambda, int32_t *iters,
+                        double *relres, int32_t *status, int warm, sspcg_stream stream) {
+  return pipeline_solve(plan, A, B, qd, rd, gamma, PD, PE, lambda, iters, relres, status, warm, stream);
+}
+}  // namespace host
+}  // namespace sspcg

@@ -50,6 +50,18 @@ _lib = None
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 
 
+class Adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
+def adam(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8) -> Adam:
+    return Adam(lr, beta1, beta2, eps)
+
+
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 1344, 256, 32, 418336
+
+
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
@@ -85,6 +97,18 @@ def lib() -> ctypes.CDLL:
             "sspcg_pipeline_batched": [_VP, _I32] + [_VP] * 14,
             "sspcg_pipeline_host": [_VP, _I32] + [_VP] * 10,
             "sspcg_solve_qp_batched_noalloc": [_I32] + [_VP] * 11 + [ctypes.POINTER(Options)] + [_VP] * 4,
+            "sspcg_mlp_create": [ctypes.POINTER(_VP), _I32],
+            "sspcg_mlp_destroy": [_VP],
+            "sspcg_mlp_set_params": [_VP, _VP, _VP],
+            "sspcg_mlp_get_params": [_VP, _VP, _VP],
+            "sspcg_mlp_get_grads": [_VP, _VP, _VP],
+            "sspcg_mlp_set_normalisation": [_VP, _VP, _VP, _VP],
+            "sspcg_mlp_get_normalisation": [_VP, _VP, _VP, _VP],
+            "sspcg_mlp_fit_normalisation": [_VP] * 9,
+            "sspcg_mlp_features": [_VP, _VP, _I32, _I32] + [_VP] * 8,
+            "sspcg_mlp_infer": [_VP] * 10,
+            "sspcg_mlp_train_step": [_VP, _VP, _I32, _I32] + [_VP] * 9 + [ctypes.POINTER(Adam), _VP, _VP],
+            "sspcg_pipeline_warm_batched": [_VP, _VP, _I32] + [_VP] * 14,
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -322,6 +346,81 @@ def sspcg_solve_qp_batched_noalloc(N, nx, nu, A, B, qd, rd, PD, PE, gamma, lam, 
                                                 _ptr(B), _ptr(qd), _ptr(rd), _ptr(PD), _ptr(PE), _ptr(gamma),
                                                 _ptr(lam), ctypes.byref(opts), _ptr(iters), _ptr(relres),
                                                 _ptr(status), _stream(stream)), "sspcg_solve_qp_batched_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# Learned warm start
+# ---------------------------------------------------------------------------
+class Mlp:
+    """Owner of an ``sspcg_mlp`` network object (parameters, Adam state, workspace)."""
+
+    def __init__(self, max_rows: int):
+        h = _VP()
+        _check(lib().sspcg_mlp_create(ctypes.byref(h), int(max_rows)), "sspcg_mlp_create")
+        self.handle, self.max_rows = h, int(max_rows)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.sspcg_mlp_destroy(self.handle)
+            self.handle = None
+
+
+def sspcg_mlp_create(max_rows: int) -> Mlp:
+    return Mlp(max_rows)
+
+
+def sspcg_mlp_set_params(mlp: Mlp, params, stream=None):
+    _check(lib().sspcg_mlp_set_params(mlp.handle, _ptr(params), _stream(stream)), "sspcg_mlp_set_params")
+
+
+def sspcg_mlp_get_params(mlp: Mlp, params, stream=None):
+    _check(lib().sspcg_mlp_get_params(mlp.handle, _ptr(params), _stream(stream)), "sspcg_mlp_get_params")
+
+
+def sspcg_mlp_get_grads(mlp: Mlp, grads, stream=None):
+    _check(lib().sspcg_mlp_get_grads(mlp.handle, _ptr(grads), _stream(stream)), "sspcg_mlp_get_grads")
+
+
+def sspcg_mlp_set_normalisation(mlp: Mlp, mu, inv_sigma, stream=None):
+    _check(lib().sspcg_mlp_set_normalisation(mlp.handle, _ptr(mu), _ptr(inv_sigma), _stream(stream)),
+           "sspcg_mlp_set_normalisation")
+
+
+def sspcg_mlp_get_normalisation(mlp: Mlp, mu, inv_sigma, stream=None):
+    _check(lib().sspcg_mlp_get_normalisation(mlp.handle, _ptr(mu), _ptr(inv_sigma), _stream(stream)),
+           "sspcg_mlp_get_normalisation")
+
+
+def sspcg_mlp_fit_normalisation(mlp: Mlp, plan: Plan, A, B, qd, rd, gamma, PD, stream=None):
+    _check(lib().sspcg_mlp_fit_normalisation(mlp.handle, plan.handle, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd),
+                                             _ptr(gamma), _ptr(PD), _stream(stream)), "sspcg_mlp_fit_normalisation")
+
+
+def sspcg_mlp_features(mlp: Mlp, plan: Plan, p_begin, p_end, A, B, qd, rd, gamma, PD, X, stream=None):
+    """X: device tensor (torch.bfloat16 or int16/uint16 bit patterns) of rows x MLP_IN."""
+    _check(lib().sspcg_mlp_features(mlp.handle, plan.handle, int(p_begin), int(p_end), _ptr(A), _ptr(B), _ptr(qd),
+                                    _ptr(rd), _ptr(gamma), _ptr(PD), _ptr(X), _stream(stream)), "sspcg_mlp_features")
+
+
+def sspcg_mlp_infer(mlp: Mlp, plan: Plan, A, B, qd, rd, gamma, PD, lam0, stream=None):
+    _check(lib().sspcg_mlp_infer(mlp.handle, plan.handle, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(gamma),
+                                 _ptr(PD), _ptr(lam0), _stream(stream)), "sspcg_mlp_infer")
+
+
+def sspcg_mlp_train_step(mlp: Mlp, plan: Plan, p_begin, p_end, A, B, qd, rd, gamma, D, E, PD, lam_star,
+                         hyper: Adam, loss, stream=None):
+    _check(lib().sspcg_mlp_train_step(mlp.handle, plan.handle, int(p_begin), int(p_end), _ptr(A), _ptr(B), _ptr(qd),
+                                      _ptr(rd), _ptr(gamma), _ptr(D), _ptr(E), _ptr(PD), _ptr(lam_star),
+                                      ctypes.byref(hyper), _ptr(loss), _stream(stream)), "sspcg_mlp_train_step")
+
+
+def sspcg_pipeline_warm_batched(plan: Plan, mlp: Mlp, kind, A, B, qd, rd, gamma, D, E, PD, PE, lam, iters, relres,
+                                status, stream=None):
+    k = PRECOND[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().sspcg_pipeline_warm_batched(plan.handle, mlp.handle, k, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd),
+                                             _ptr(gamma), _ptr(D), _ptr(E), _ptr(PD), _ptr(PE), _ptr(lam),
+                                             _ptr(iters), _ptr(relres), _ptr(status), _stream(stream)),
+           "sspcg_pipeline_warm_batched")
 
 
 # ---------------------------------------------------------------------------
