@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--impl", default="sspcg", choices=["sspcg", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target duration of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="first N problems of the workload only (small profiler captures); 0: all")
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
+    ap.add_argument("--train-problems", type=int, default=4096, help="training problems of the warm-start network")
+    ap.add_argument("--train-epochs", type=int, default=6)
     return ap.parse_args()
 
 
@@ -160,6 +165,85 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def train_warm_start(args, torch, sspcg, rank):
+    """Train the warm-start network (untimed) on plain solves of the manipulator-like and ragged-batch
+    generators; returns the network and its loss history."""
+    half = max(1, args.train_problems // 2)
+    base = (1 << 20) + rank * args.train_problems  # disjoint from every rank's benchmark problems
+    train = [P.make_problem(P.config_key(2, base + i), 64, 14, 7, 0.01) for i in range(half)]
+    train += P.make_workload(P.RAGGED_BATCH_4096, count=half, start=base)
+    plan = sspcg.sspcg_plan_create([p.N for p in train], [p.nx for p in train], [p.nu for p in train],
+                                   sspcg.options(tol=1e-6))
+    b = sspcg.Batch(plan, train)
+    b.pipeline(PRECOND)
+    d = b.dev
+    net = sspcg.sspcg_mlp_create(8192)
+    sspcg.sspcg_mlp_fit_normalisation(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD)
+    sspcg.sspcg_mlp_set_params(net, torch.from_numpy(P.mlp_initial_params(0)).cuda())
+    chunk = 32
+    starts = list(range(0, plan.nprob, chunk))
+    rng = np.random.default_rng(0)
+    loss = torch.zeros(len(starts), dtype=torch.float64, device="cuda")
+    lam_star = b.lam.clone()
+    hist = []
+    for _ in range(args.train_epochs):
+        for j, s0 in enumerate(rng.permutation(starts)):
+            sspcg.sspcg_mlp_train_step(net, plan, int(s0), min(int(s0) + chunk, plan.nprob), d["A"], d["B"], d["qd"],
+                                       d["rd"], d["gamma"], b.D, b.E, b.PD, lam_star, sspcg.adam(), loss[j:j + 1])
+        hist.append(float(loss.mean().item()))
+    return net, hist, len(train)
+
+
+def warm_start_comparison(args, torch, sspcg, stream, rank):
+    """Held-out warm-start workload (4096 problems, nx = 14, N = 64, h = 0.01): the whole path from lambda0 = 0
+    against the whole path started from the trained network (inference inside the timed step), same GPU."""
+    t0 = time.time()
+    net, hist, ntrain = train_warm_start(args, torch, sspcg, rank)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    w = P.WARMSTART_EVAL_4096
+    probs = P.make_workload(w, count=w.nprob, start=rank * w.nprob)
+    plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
+                                   sspcg.options(tol=w.tol))
+    b = sspcg.Batch(plan, probs)
+    d = b.dev
+
+    def plain():
+        sspcg.sspcg_pipeline_batched(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD,
+                                     b.PE, b.lam, b.iters, b.relres, b.status, stream)
+
+    def warm():
+        sspcg.sspcg_pipeline_warm_batched(plan, net, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E,
+                                          b.PD, b.PE, b.lam, b.iters, b.relres, b.status, stream)
+
+    out = {}
+    for name, fn in (("plain", plain), ("warm", warm)):
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        it = b.iters.cpu().numpy()
+        ok = bool((b.status.cpu().numpy() == 0).all() and (b.relres.cpu().numpy() <= w.tol).all())
+        out[name] = {"solves_per_s": len(probs) / (ms / 1e3), "ms_per_step": ms, "iters_mean": float(it.mean()),
+                     "iters_p50": float(np.percentile(it, 50)), "all_converged": ok}
+    stats = sspcg.plan_stats(plan)
+    launches_plain = 3 + (3 if stats["pipeline_f64"] else 0) + stats["pipeline_launches"]
+    # inference per chunk of 8192 rows: features + 3 products + scatter
+    chunks = -(-sum(p.n for p in probs) // 8192)
+    return {"workload": w.name, "train_problems": ntrain, "train_epochs": args.train_epochs,
+            "train_loss": [round(x, 4) for x in hist], "train_seconds": round(train_s, 2),
+            "plain": out["plain"], "warm": out["warm"],
+            "speedup": out["warm"]["solves_per_s"] / out["plain"]["solves_per_s"],
+            "gpu_launches": args.steps * (2 * launches_plain + 5 * chunks)}
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
@@ -176,7 +260,7 @@ def main():
     from paper_2309_06427_gb300 import sspcg
 
     w = WORKLOAD
-    nprob = w.nprob
+    nprob = args.problems if args.problems > 0 else w.nprob
     probs = P.make_workload(w, count=nprob, start=rank * nprob)  # weak scaling: each rank its own problems
     opts = sspcg.options(tol=w.tol)
     plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs], opts)
@@ -286,6 +370,8 @@ def main():
                          "fp64_problems": stats["pipeline_f64"],
                          "pcg_launches_per_step": stats["pipeline_launches"]}
     line["build_ms_per_step"] = statistics.mean(build_ms)
+    if not args.no_warm_start:
+        line["warm_start"] = warm_start_comparison(args, torch, sspcg, stream, rank)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(probs, args.cpu_seconds, w.tol)
     print(json.dumps(line), flush=True)
