@@ -408,10 +408,20 @@ typedef struct {
   float eps;   /* denominator guard */
 } sspcg_adam;
 
+/* Engines of the forward products (inference and the training forward pass; the backward products
+ * always use mma.sync):
+ *   SSPCG_MLP_ENGINE_TCGEN05  tcgen05.mma with TMEM accumulators, operands staged by TMA (default)
+ *   SSPCG_MLP_ENGINE_MMA_SYNC mma.sync.m16n8k16 with register accumulators */
+enum { SSPCG_MLP_ENGINE_TCGEN05 = 0, SSPCG_MLP_ENGINE_MMA_SYNC = 1 };
+
 /* Create a network with workspace for max_rows >= 1 knot rows per call chunk.
  * Parameters start at zero; normalisation at mu = 0, inv_sigma = 1. */
 sspcg_status sspcg_mlp_create(sspcg_mlp **mlp, int32_t max_rows);
 sspcg_status sspcg_mlp_destroy(sspcg_mlp *mlp);
+/* Select the forward-product engine; SSPCG_ERR_UNSUPPORTED when TMA descriptors cannot be made. */
+sspcg_status sspcg_mlp_set_engine(sspcg_mlp *mlp, int32_t engine);
+/* Synchronous: *flag = 1 if a tensor-core product gave up on a bounded wait since creation, else 0. */
+sspcg_status sspcg_mlp_status(const sspcg_mlp *mlp, int32_t *flag);
 /* Copy SSPCG_MLP_PARAMS FP32 values from a device array into the network and reset the Adam state. */
 sspcg_status sspcg_mlp_set_params(sspcg_mlp *mlp, const float *params, sspcg_stream stream);
 /* Copy the FP32 parameters (or the gradients of the last training step) to a device array. */

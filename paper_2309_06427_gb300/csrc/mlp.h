@@ -46,6 +46,12 @@ enum Epilogue : int { kEpiBiasRelu = 0, kEpiBiasF32 = 1, kEpiMask = 2 };
 // C[M][N] = epilogue(A[M][K] B[N][K]^T) with bf16 operands and FP32 accumulation.
 cudaError_t launch_gemm_nt(int epi, const bf16 *A, const bf16 *B, int64_t M, int N, int K, const float *bias,
                            const bf16 *mask, bf16 *Cb, float *Cf, cudaStream_t st);
+// The same product on the 5th-generation tensor cores (tcgen05 + TMA): N in {256, 32}, K % 64 == 0,
+// epilogues kEpiBiasRelu and kEpiBiasF32; *err is set to 1 when a bounded wait expires.
+cudaError_t launch_gemm_nt_tc(int epi, const bf16 *A, const bf16 *B, int64_t M, int N, int K, const float *bias,
+                              bf16 *Cb, float *Cf, int *err, cudaStream_t st);
+// False when the driver's tensor-map encoder is unavailable.
+bool tc_available();
 // part[s][N1][N2] = sum over rows m of split s of G[m][n1] X[m][n2].
 cudaError_t launch_gemm_tn(const bf16 *G, int N1, const bf16 *X, int N2, int64_t M, float *part, cudaStream_t st);
 int64_t gemm_tn_splits(int64_t M);

@@ -27,6 +27,8 @@ struct sspcg_mlp {
   float *part = nullptr;  // split partial sums of the gradient products
   double *stat_part = nullptr;
   int stat_warps = 0;
+  int engine = SSPCG_MLP_ENGINE_TCGEN05;
+  int *err = nullptr;  // device: set by a tensor-core product whose bounded wait expired
 };
 
 namespace {
@@ -42,7 +44,7 @@ void mlp_free(sspcg_mlp *n) {
   for (void *p : {(void *)n->w, (void *)n->g, (void *)n->m, (void *)n->v, (void *)n->W1b, (void *)n->W2b,
                   (void *)n->W3b, (void *)n->W2t, (void *)n->W3t, (void *)n->mu, (void *)n->isd, (void *)n->X,
                   (void *)n->H1, (void *)n->H2, (void *)n->dY, (void *)n->dH2, (void *)n->dH1, (void *)n->Y,
-                  (void *)n->U, (void *)n->uu, (void *)n->gg, (void *)n->part, (void *)n->stat_part})
+                  (void *)n->U, (void *)n->uu, (void *)n->gg, (void *)n->part, (void *)n->stat_part, (void *)n->err})
     cudaFree(p);
   delete n;
 }
@@ -77,6 +79,12 @@ sspcg_status forward(sspcg_mlp *n, const host::PlanView &v, int64_t row0, int64_
                      cudaStream_t st) {
   RowSpan rs{v.ps, v.kref, row0, rows};
   MLP_CUDA(launch_features(rs, q, n->mu, n->isd, n->X, st));
+  if (n->engine == SSPCG_MLP_ENGINE_TCGEN05) {
+    MLP_CUDA(launch_gemm_nt_tc(kEpiBiasRelu, n->X, n->W1b, rows, kHid, kIn, n->w + kB1, n->H1, nullptr, n->err, st));
+    MLP_CUDA(launch_gemm_nt_tc(kEpiBiasRelu, n->H1, n->W2b, rows, kHid, kHid, n->w + kB2, n->H2, nullptr, n->err, st));
+    MLP_CUDA(launch_gemm_nt_tc(kEpiBiasF32, n->H2, n->W3b, rows, kOut, kHid, n->w + kB3, nullptr, n->Y, n->err, st));
+    return SSPCG_OK;
+  }
   MLP_CUDA(launch_gemm_nt(kEpiBiasRelu, n->X, n->W1b, rows, kHid, kIn, n->w + kB1, nullptr, n->H1, nullptr, st));
   MLP_CUDA(launch_gemm_nt(kEpiBiasRelu, n->H1, n->W2b, rows, kHid, kHid, n->w + kB2, nullptr, n->H2, nullptr, st));
   MLP_CUDA(launch_gemm_nt(kEpiBiasF32, n->H2, n->W3b, rows, kOut, kHid, n->w + kB3, nullptr, nullptr, n->Y, st));
@@ -118,7 +126,10 @@ sspcg_status sspcg_mlp_create(sspcg_mlp **out, int32_t max_rows) {
   alloc(&n->Y, R * kOut); alloc(&n->U, R * kOut);
   alloc(&n->uu, R); alloc(&n->gg, R);
   alloc(&n->part, part_floats(R));
+  alloc(&n->err, 1);
   if (e != cudaSuccess) return fail(e);
+  if ((e = cudaMemset(n->err, 0, sizeof(int))) != cudaSuccess) return fail(e);
+  if (!tc_available()) n->engine = SSPCG_MLP_ENGINE_MMA_SYNC;
   for (float *p : {n->w, n->g, n->m, n->v})
     if ((e = cudaMemset(p, 0, sizeof(float) * kParams)) != cudaSuccess) return fail(e);
   if ((e = cudaMemset(n->mu, 0, sizeof(float) * kIn)) != cudaSuccess) return fail(e);
@@ -133,6 +144,21 @@ sspcg_status sspcg_mlp_create(sspcg_mlp **out, int32_t max_rows) {
 
 sspcg_status sspcg_mlp_destroy(sspcg_mlp *mlp) {
   mlp_free(mlp);
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_mlp_set_engine(sspcg_mlp *n, int32_t engine) {
+  if (!n || (engine != SSPCG_MLP_ENGINE_TCGEN05 && engine != SSPCG_MLP_ENGINE_MMA_SYNC)) return SSPCG_ERR_INVALID_ARG;
+  if (engine == SSPCG_MLP_ENGINE_TCGEN05 && !tc_available()) return SSPCG_ERR_UNSUPPORTED;
+  n->engine = engine;
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_mlp_status(const sspcg_mlp *n, int32_t *flag) {
+  if (!n || !flag) return SSPCG_ERR_INVALID_ARG;
+  int v = 0;
+  MLP_CUDA(cudaMemcpy(&v, n->err, sizeof(int), cudaMemcpyDeviceToHost));
+  *flag = v;
   return SSPCG_OK;
 }
 

@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
             "sspcg_mlp_create": [ctypes.POINTER(_VP), _I32],
             "sspcg_mlp_destroy": [_VP],
             "sspcg_mlp_set_params": [_VP, _VP, _VP],
+            "sspcg_mlp_set_engine": [_VP, _I32],
+            "sspcg_mlp_status": [_VP, _VP],
             "sspcg_mlp_get_params": [_VP, _VP, _VP],
             "sspcg_mlp_get_grads": [_VP, _VP, _VP],
             "sspcg_mlp_set_normalisation": [_VP, _VP, _VP, _VP],
@@ -367,6 +369,20 @@ class Mlp:
 
 def sspcg_mlp_create(max_rows: int) -> Mlp:
     return Mlp(max_rows)
+
+
+MLP_ENGINE = {"tcgen05": 0, "mma_sync": 1}
+
+
+def sspcg_mlp_set_engine(mlp: Mlp, engine="tcgen05"):
+    e = MLP_ENGINE[engine] if isinstance(engine, str) else int(engine)
+    _check(lib().sspcg_mlp_set_engine(mlp.handle, e), "sspcg_mlp_set_engine")
+
+
+def sspcg_mlp_status(mlp: Mlp) -> int:
+    v = ctypes.c_int32(0)
+    _check(lib().sspcg_mlp_status(mlp.handle, ctypes.byref(v)), "sspcg_mlp_status")
+    return int(v.value)
 
 
 def sspcg_mlp_set_params(mlp: Mlp, params, stream=None):

@@ -102,9 +102,11 @@ def test_normalisation_fit_matches_oracle():
     assert np.allclose(isd[live], isd_o[live], rtol=1e-4)
 
 
-def test_forward_matches_oracle():
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
+def test_forward_matches_oracle(engine):
     probs = _problems()
     plan, b, net = _setup(probs)
+    sspcg.sspcg_mlp_set_engine(net, engine)
     Ss, F = _oracle_features(probs)
     mu, isd = _set_norm(net, *omlp.normalisation(F))
     flat32, prm = _random_params(7)
@@ -119,6 +121,37 @@ def test_forward_matches_oracle():
     # FP32 accumulation order and rare bfloat16 rounding flips of hidden activations
     for g, r in zip(got, ref):
         assert rel(g, r) <= 2e-3
+    assert rel(np.concatenate([g.ravel() for g in got]), np.concatenate([r.ravel() for r in ref])) <= 5e-4
+    assert sspcg.sspcg_mlp_status(net) == 0
+
+
+def test_engines_agree_over_many_tiles_and_chunks():
+    """Inference over ~9,000 knot rows in chunks of 1,000 (ragged tails in every 128-row tile grid)."""
+    probs = P.make_workload(P.RAGGED_BATCH_4096, count=120, start=500)
+    plan, b, net = _setup(probs, max_rows=1000)
+    Ss, F = _oracle_features(probs[:6])
+    d = b.dev
+    sspcg.sspcg_mlp_fit_normalisation(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD)
+    flat32, prm = _random_params(3)
+    sspcg.sspcg_mlp_set_params(net, torch.from_numpy(flat32).cuda())
+    out = {}
+    for engine in ("tcgen05", "mma_sync"):
+        sspcg.sspcg_mlp_set_engine(net, engine)
+        lam0 = plan.empty(sspcg.ARRAY_VEC)
+        sspcg.sspcg_mlp_infer(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD, lam0)
+        torch.cuda.synchronize()
+        out[engine] = lam0.cpu().numpy().astype(np.float64)
+    assert sspcg.sspcg_mlp_status(net) == 0
+    assert np.isfinite(out["tcgen05"]).all() and np.abs(out["tcgen05"]).max() > 0
+    assert rel(out["tcgen05"], out["mma_sync"]) <= 5e-4
+    # the first problems against the oracle, with the normalisation the GPU fitted
+    mu = torch.zeros(omlp.D_IN, device="cuda"); isd = torch.zeros(omlp.D_IN, device="cuda")
+    sspcg.sspcg_mlp_get_normalisation(net, mu, isd)
+    torch.cuda.synchronize()
+    X = omlp.normalise(F, mu.cpu().numpy().astype(np.float64), isd.cpu().numpy().astype(np.float64))
+    ref = omlp.warm_start(prm, X, [p.nx for p in probs[:6]], [p.n for p in probs[:6]])
+    got = plan.unpack(sspcg.ARRAY_VEC, torch.from_numpy(out["tcgen05"].astype(np.float32)),
+                      [p.gamma.shape for p in probs])[:6]
     assert rel(np.concatenate([g.ravel() for g in got]), np.concatenate([r.ravel() for r in ref])) <= 5e-4
 
 
