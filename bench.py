@@ -33,6 +33,8 @@ UNIT = "solves/s"
 WORKLOAD = P.RAGGED_BATCH_4096
 PRECOND = "sym"
 SMEM_BYTES_PER_CLK_PER_SM = 128  # shared-memory bandwidth of one SM (32 banks x 4 B per clock)
+MLP_FLOP_PER_ROW = 2 * (1344 * 256 + 256 * 256 + 256 * 32)  # warm-start network forward, one knot row
+MLP_MAX_ROWS = 1 << 19  # network workspace: the whole warm-start batch (266,240 knot rows) in one chunk
 
 
 def parse():
@@ -177,7 +179,7 @@ def train_warm_start(args, torch, sspcg, rank):
     b = sspcg.Batch(plan, train)
     b.pipeline(PRECOND)
     d = b.dev
-    net = sspcg.sspcg_mlp_create(8192)
+    net = sspcg.sspcg_mlp_create(MLP_MAX_ROWS)
     sspcg.sspcg_mlp_fit_normalisation(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD)
     sspcg.sspcg_mlp_set_params(net, torch.from_numpy(P.mlp_initial_params(0)).cuda())
     chunk = 32
@@ -233,13 +235,34 @@ def warm_start_comparison(args, torch, sspcg, stream, rank):
         ok = bool((b.status.cpu().numpy() == 0).all() and (b.relres.cpu().numpy() <= w.tol).all())
         out[name] = {"solves_per_s": len(probs) / (ms / 1e3), "ms_per_step": ms, "iters_mean": float(it.mean()),
                      "iters_p50": float(np.percentile(it, 50)), "all_converged": ok}
+    # inference alone (features + three products + scatter), each product engine
+    b.pipeline(PRECOND, stream)
+    lam0 = plan.empty(sspcg.ARRAY_VEC)
+    rows = sum(p.n for p in probs)
+    infer = {}
+    for engine in ("tcgen05", "mma_sync"):
+        sspcg.sspcg_mlp_set_engine(net, engine)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                sspcg.sspcg_mlp_infer(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD, lam0, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sspcg.sspcg_mlp_infer(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD, lam0, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        infer[engine] = {"ms": ms, "tflops": rows * MLP_FLOP_PER_ROW / (ms / 1e3) / 1e12}
+    sspcg.sspcg_mlp_set_engine(net, "tcgen05")
     stats = sspcg.plan_stats(plan)
     launches_plain = 3 + (3 if stats["pipeline_f64"] else 0) + stats["pipeline_launches"]
-    # inference per chunk of 8192 rows: features + 3 products + scatter
-    chunks = -(-sum(p.n for p in probs) // 8192)
+    # inference per chunk of MLP_MAX_ROWS rows: features + 3 products + scatter
+    chunks = -(-sum(p.n for p in probs) // MLP_MAX_ROWS)
     return {"workload": w.name, "train_problems": ntrain, "train_epochs": args.train_epochs,
             "train_loss": [round(x, 4) for x in hist], "train_seconds": round(train_s, 2),
             "plain": out["plain"], "warm": out["warm"],
+            "inference": {"rows": rows, "flop_per_row": MLP_FLOP_PER_ROW, **infer},
             "speedup": out["warm"]["solves_per_s"] / out["plain"]["solves_per_s"],
             "gpu_launches": args.steps * (2 * launches_plain + 5 * chunks)}
 

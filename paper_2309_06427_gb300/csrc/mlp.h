@@ -18,8 +18,10 @@ constexpr int kOffA = 0, kOffB = 784, kOffQp = 1176, kOffRp = 1204, kOffQ = 1218
 // Flat FP32 parameter layout: W1 [256][1344], b1, W2 [256][256], b2, W3 [32][256], b3.
 constexpr int64_t kW1 = 0, kB1 = kW1 + (int64_t)kHid * kIn, kW2 = kB1 + kHid, kB2 = kW2 + (int64_t)kHid * kHid,
                   kW3 = kB2 + kHid, kB3 = kW3 + (int64_t)kOut * kHid, kParams = kB3 + kOut;
-// Rows of the contraction per split of a weight-gradient product.
+// Weight-gradient products split their row contraction into at most kMaxSplits chunks of at least
+// kRowsPerSplit rows, summed in a fixed order afterwards.
 constexpr int kRowsPerSplit = 512;
+constexpr int kMaxSplits = 64;
 
 using bf16 = __nv_bfloat16;
 
@@ -55,7 +57,7 @@ bool tc_available();
 // part[s][N1][N2] = sum over rows m of split s of G[m][n1] X[m][n2].
 cudaError_t launch_gemm_tn(const bf16 *G, int N1, const bf16 *X, int N2, int64_t M, float *part, cudaStream_t st);
 int64_t gemm_tn_splits(int64_t M);
-// part[chunk][N] = column sums of Y[M][N] over row chunks of kRowsPerSplit.
+// part[chunk][N] = column sums of Y[M][N] over the same row chunks as launch_gemm_tn.
 cudaError_t launch_colsum(const bf16 *Y, int64_t M, int N, float *part, cudaStream_t st);
 // out[i] = sum_s part[s][i], s in order.
 cudaError_t launch_reduce_splits(const float *part, int64_t splits, int64_t n, float *out, cudaStream_t st);

@@ -10,51 +10,85 @@ namespace mlp {
 namespace {
 
 // ---------------------------------------------------------------------------
-// Knot features.  Column pairs (c, c+1), c even, never straddle a segment or a
-// padded matrix row (all segment starts and the row lengths 28 and 14 are even).
+// Knot features.  A warp first stages its knot's data in shared memory with
+// coalesced, independent loads (A_{k-1}, B_{k-1}, D_k^-1 compact, the
+// diagonals and gamma_k), then writes the padded row from there.  Column
+// pairs (c, c+1), c even, never straddle a segment or a padded matrix row
+// (all segment starts and the row lengths 28 and 14 are even).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 feature_pair(int c, const ProbDesc &d, int k, const QpData &q, float dj0,
-                                               float dj1) {
+constexpr int kStA = 0, kStB = 784, kStPD = 1176, kStQp = 1960, kStRp = 1988, kStQ = 2002, kStG = 2030;
+constexpr int kStFloats = 2064;  // per warp (8,256 bytes)
+constexpr int kFeatWarps = 4;
+
+// dst[i] = src[i] for i < n <= MAXN: all loads issued before the stores.
+template <int MAXN>
+__device__ __forceinline__ void warp_copy(float *dst, const float *src, int n, int lane) {
+  constexpr int T = (MAXN + 31) / 32;
+  float v[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int i = lane + 32 * t;
+    v[t] = i < n ? src[i] : 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int i = lane + 32 * t;
+    if (i < n) dst[i] = v[t];
+  }
+}
+
+__device__ __forceinline__ void stage_knot(float *s, const ProbDesc &d, int k, const QpData &q, int lane) {
   const int m = d.nx, u = d.nu;
+  if (k > 0) {
+    warp_copy<kPadX * kPadX>(s + kStA, q.A + d.oA + (int64_t)(k - 1) * m * m, m * m, lane);
+    if (u > 0) {
+      warp_copy<kPadX * kPadU>(s + kStB, q.B + d.oB + (int64_t)(k - 1) * m * u, m * u, lane);
+      if (lane < u) s[kStRp + lane] = q.rd[d.orr + (int64_t)(k - 1) * u + lane];
+    }
+    if (lane < m) s[kStQp + lane] = q.qd[d.oq + (int64_t)(k - 1) * m + lane];
+  }
+  warp_copy<kPadX * kPadX>(s + kStPD, q.PD + d.odiag + (int64_t)k * m * m, m * m, lane);
+  if (lane < m) {
+    s[kStQ + lane] = q.qd[d.oq + (int64_t)k * m + lane];
+    s[kStG + lane] = q.gamma[d.ovec + (int64_t)k * m + lane];
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ float2 feature_pair(int c, int m, int u, int k, const float *s, float dj0, float dj1) {
   float2 v = make_float2(0.f, 0.f);
   if (c < kOffB) {
     const int i = c / kPadX, j = c % kPadX;
     if (k > 0 && i < m) {
-      const float *row = q.A + d.oA + (int64_t)(k - 1) * m * m + (int64_t)i * m;
-      if (j < m) v.x = row[j];
-      if (j + 1 < m) v.y = row[j + 1];
+      if (j < m) v.x = s[kStA + i * m + j];
+      if (j + 1 < m) v.y = s[kStA + i * m + j + 1];
     }
   } else if (c < kOffQp) {
     const int cc = c - kOffB, i = cc / kPadU, j = cc % kPadU;
-    if (k > 0 && u > 0 && i < m) {
-      const float *row = q.B + d.oB + (int64_t)(k - 1) * m * u + (int64_t)i * u;
-      if (j < u) v.x = row[j];
-      if (j + 1 < u) v.y = row[j + 1];
+    if (k > 0 && i < m) {
+      if (j < u) v.x = s[kStB + i * u + j];
+      if (j + 1 < u) v.y = s[kStB + i * u + j + 1];
     }
   } else if (c < kOffRp) {
     const int i = c - kOffQp;
     if (k > 0) {
-      const float *s = q.qd + d.oq + (int64_t)(k - 1) * m;
-      if (i < m) v.x = s[i];
-      if (i + 1 < m) v.y = s[i + 1];
+      if (i < m) v.x = s[kStQp + i];
+      if (i + 1 < m) v.y = s[kStQp + i + 1];
     }
   } else if (c < kOffQ) {
     const int i = c - kOffRp;
-    if (k > 0 && u > 0) {
-      const float *s = q.rd + d.orr + (int64_t)(k - 1) * u;
-      if (i < u) v.x = s[i];
-      if (i + 1 < u) v.y = s[i + 1];
+    if (k > 0) {
+      if (i < u) v.x = s[kStRp + i];
+      if (i + 1 < u) v.y = s[kStRp + i + 1];
     }
   } else if (c < kOffG) {
     const int i = c - kOffQ;
-    const float *s = q.qd + d.oq + (int64_t)k * m;
-    if (i < m) v.x = s[i];
-    if (i + 1 < m) v.y = s[i + 1];
+    if (i < m) v.x = s[kStQ + i];
+    if (i + 1 < m) v.y = s[kStQ + i + 1];
   } else if (c < kOffDj) {
     const int i = c - kOffG;
-    const float *s = q.gamma + d.ovec + (int64_t)k * m;
-    if (i < m) v.x = s[i];
-    if (i + 1 < m) v.y = s[i + 1];
+    if (i < m) v.x = s[kStG + i];
+    if (i + 1 < m) v.y = s[kStG + i + 1];
   } else if (c < kOffNx) {
     v.x = dj0;
     v.y = dj1;
@@ -64,41 +98,43 @@ __device__ __forceinline__ float2 feature_pair(int c, const ProbDesc &d, int k, 
   return v;
 }
 
-// D_k^-1 gamma_k, component ``lane`` (zero for lane >= nx): PD holds D_k^-1.
-__device__ __forceinline__ float block_solve(const ProbDesc &d, int k, const QpData &q, int lane) {
-  const int m = d.nx;
-  float s = 0.f;
+// D_k^-1 gamma_k, component ``lane`` (zero for lane >= nx), from the staged PD block and gamma.
+__device__ __forceinline__ float block_solve(const float *s, int m, int lane) {
+  float acc = 0.f;
   if (lane < m) {
-    const float *P = q.PD + d.odiag + (int64_t)k * m * m + (int64_t)lane * m;
-    const float *g = q.gamma + d.ovec + (int64_t)k * m;
-    for (int j = 0; j < m; ++j) s = fmaf(P[j], g[j], s);
+    const float *P = s + kStPD + lane * m;
+    for (int j = 0; j < m; ++j) acc = fmaf(P[j], s[kStG + j], acc);
   }
-  return s;
+  return acc;
 }
 
 constexpr int kPairIters = kIn / 64;  // 21 column pairs per lane
 
 // One warp per knot row; lane l writes columns 64 i + 2 l, +1.
-__global__ void __launch_bounds__(256) features_kernel(RowSpan rs, QpData q, const float *__restrict__ mu,
-                                                       const float *__restrict__ isd, bf16 *__restrict__ X) {
-  const int lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= rs.nrows) return;
+__global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(RowSpan rs, QpData q, const float *__restrict__ mu,
+                                                                   const float *__restrict__ isd,
+                                                                   bf16 *__restrict__ X) {
+  __shared__ __align__(16) float stage[kFeatWarps][kStFloats];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t r = (int64_t)blockIdx.x * kFeatWarps + wl;
+  if (r >= rs.nrows) return;  // warp-uniform
   const int2 ref = rs.kref[rs.row0 + r];
   const ProbDesc d = rs.ps.get(ref.x);
-  const int k = ref.y;
-  const float dj = block_solve(d, k, q, lane);
+  const int k = ref.y, m = d.nx, u = d.nu;
+  float *s = stage[wl];
+  stage_knot(s, d, k, q, lane);
+  const float dj = block_solve(s, m, lane);
   __nv_bfloat162 *out = reinterpret_cast<__nv_bfloat162 *>(X + r * kIn);
-#pragma unroll 1
+#pragma unroll
   for (int it = 0; it < kPairIters; ++it) {
     const int c = it * 64 + 2 * lane;
     float dj0 = 0.f, dj1 = 0.f;
-    if (it >= kOffDj / 64) {  // warp-uniform: iterations that may cover the D^-1 gamma slot
-      const int s = min(max(c - kOffDj, 0), 30);
-      dj0 = __shfl_sync(0xffffffffu, dj, s);
-      dj1 = __shfl_sync(0xffffffffu, dj, s + 1);
+    if (it >= kOffDj / 64) {  // iterations that may cover the D^-1 gamma slot
+      const int sidx = min(max(c - kOffDj, 0), 30);
+      dj0 = __shfl_sync(0xffffffffu, dj, sidx);
+      dj1 = __shfl_sync(0xffffffffu, dj, sidx + 1);
     }
-    float2 v = feature_pair(c, d, k, q, dj0, dj1);
+    float2 v = feature_pair(c, m, u, k, s, dj0, dj1);
     v.x = (v.x - mu[c]) * isd[c];
     v.y = (v.y - mu[c + 1]) * isd[c + 1];
     out[c >> 1] = __floats2bfloat162_rn(v.x, v.y);
@@ -106,18 +142,23 @@ __global__ void __launch_bounds__(256) features_kernel(RowSpan rs, QpData q, con
 }
 
 // Per-warp FP64 column sums and sums of squares of the raw features.
-__global__ void __launch_bounds__(256) feature_stats_kernel(RowSpan rs, QpData q, double *__restrict__ part) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  double s[kPairIters][2], ss[kPairIters][2];
+__global__ void __launch_bounds__(kFeatWarps * 32) feature_stats_kernel(RowSpan rs, QpData q,
+                                                                        double *__restrict__ part) {
+  __shared__ __align__(16) float stage[kFeatWarps][kStFloats];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * kFeatWarps + wl;
+  const int64_t nw = (int64_t)gridDim.x * kFeatWarps;
+  float *s = stage[wl];
+  double sm[kPairIters][2], ss[kPairIters][2];
 #pragma unroll
-  for (int it = 0; it < kPairIters; ++it) s[it][0] = s[it][1] = ss[it][0] = ss[it][1] = 0.0;
+  for (int it = 0; it < kPairIters; ++it) sm[it][0] = sm[it][1] = ss[it][0] = ss[it][1] = 0.0;
   for (int64_t r = w; r < rs.nrows; r += nw) {
     const int2 ref = rs.kref[rs.row0 + r];
     const ProbDesc d = rs.ps.get(ref.x);
-    const int k = ref.y;
-    const float dj = block_solve(d, k, q, lane);
+    const int k = ref.y, m = d.nx, u = d.nu;
+    __syncwarp();  // the previous row's reads of the stage are done
+    stage_knot(s, d, k, q, lane);
+    const float dj = block_solve(s, m, lane);
 #pragma unroll
     for (int it = 0; it < kPairIters; ++it) {
       const int c = it * 64 + 2 * lane;
@@ -127,8 +168,8 @@ __global__ void __launch_bounds__(256) feature_stats_kernel(RowSpan rs, QpData q
         dj0 = __shfl_sync(0xffffffffu, dj, sidx);
         dj1 = __shfl_sync(0xffffffffu, dj, sidx + 1);
       }
-      const float2 v = feature_pair(c, d, k, q, dj0, dj1);
-      s[it][0] += v.x; s[it][1] += v.y;
+      const float2 v = feature_pair(c, m, u, k, s, dj0, dj1);
+      sm[it][0] += v.x; sm[it][1] += v.y;
       ss[it][0] += (double)v.x * v.x; ss[it][1] += (double)v.y * v.y;
     }
   }
@@ -136,7 +177,7 @@ __global__ void __launch_bounds__(256) feature_stats_kernel(RowSpan rs, QpData q
 #pragma unroll
   for (int it = 0; it < kPairIters; ++it) {
     const int c = it * 64 + 2 * lane;
-    o[c] = s[it][0]; o[c + 1] = s[it][1];
+    o[c] = sm[it][0]; o[c + 1] = sm[it][1];
     o[kIn + c] = ss[it][0]; o[kIn + c + 1] = ss[it][1];
   }
 }
@@ -302,7 +343,7 @@ __global__ void __launch_bounds__(WM *WN * 32) gemm_nt_kernel(const bf16 *__rest
 // part[s][N1][N2] = sum over the rows m of split s of G[m][n1] X[m][n2]; 4 warps as 2 x 2.
 template <int BM, int BN>
 __global__ void __launch_bounds__(128) gemm_tn_kernel(const bf16 *__restrict__ G, int N1, const bf16 *__restrict__ X,
-                                                      int N2, int64_t M, float *__restrict__ part) {
+                                                      int N2, int64_t M, int64_t rps, float *__restrict__ part) {
   constexpr int TM = BM / 2, TN = BN / 2, MT = TM / 16, NT = TN / 8;
   constexpr int LA = BM + 8, LB = BN + 8;
   __shared__ __align__(128) bf16 Gs[2][kBK][LA];
@@ -310,8 +351,8 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const bf16 *__restrict__ G
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 1, wn = warp >> 1;
   const int n2_0 = blockIdx.x * BN, n1_0 = blockIdx.y * BM;
-  const int64_t r_begin = (int64_t)blockIdx.z * kRowsPerSplit;
-  const int64_t r_end = r_begin + kRowsPerSplit < M ? r_begin + kRowsPerSplit : M;
+  const int64_t r_begin = (int64_t)blockIdx.z * rps;
+  const int64_t r_end = r_begin + rps < M ? r_begin + rps : M;
   const int KT = (int)((r_end - r_begin + kBK - 1) / kBK);
 
   auto load = [&](int stage, int64_t r0) {
@@ -386,10 +427,10 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const bf16 *__restrict__ G
     }
 }
 
-__global__ void colsum_kernel(const bf16 *__restrict__ Y, int64_t M, int N, float *__restrict__ part) {
+__global__ void colsum_kernel(const bf16 *__restrict__ Y, int64_t M, int N, int64_t rps, float *__restrict__ part) {
   const int c = threadIdx.x;
-  const int64_t r0 = (int64_t)blockIdx.x * kRowsPerSplit;
-  const int64_t r1 = r0 + kRowsPerSplit < M ? r0 + kRowsPerSplit : M;
+  const int64_t r0 = (int64_t)blockIdx.x * rps;
+  const int64_t r1 = r0 + rps < M ? r0 + rps : M;
   float s = 0.f;
   for (int64_t r = r0; r < r1; ++r) s += __bfloat162float(Y[r * N + c]);
   part[(int64_t)blockIdx.x * N + c] = s;
@@ -541,14 +582,14 @@ int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 cudaError_t launch_features(const RowSpan &rs, const QpData &q, const float *mu, const float *isd, bf16 *X,
                             cudaStream_t st) {
   if (rs.nrows <= 0) return cudaSuccess;
-  features_kernel<<<(unsigned)cdiv64(rs.nrows, 8), 256, 0, st>>>(rs, q, mu, isd, X);
+  features_kernel<<<(unsigned)cdiv64(rs.nrows, kFeatWarps), kFeatWarps * 32, 0, st>>>(rs, q, mu, isd, X);
   return cudaGetLastError();
 }
 
 int feature_stats_warps(int sms) { return sms * 8 * 2; }
 
 cudaError_t launch_feature_stats(const RowSpan &rs, const QpData &q, double *part, int warps, cudaStream_t st) {
-  feature_stats_kernel<<<warps / 8, 256, 0, st>>>(rs, q, part);
+  feature_stats_kernel<<<warps / kFeatWarps, kFeatWarps * 32, 0, st>>>(rs, q, part);
   return cudaGetLastError();
 }
 
@@ -580,16 +621,23 @@ cudaError_t launch_gemm_nt(int epi, const bf16 *A, const bf16 *B, int64_t M, int
   return cudaErrorInvalidValue;
 }
 
-int64_t gemm_tn_splits(int64_t M) { return M > 0 ? cdiv64(M, kRowsPerSplit) : 0; }
+int64_t gemm_tn_splits(int64_t M) { return M > 0 ? std::min<int64_t>(cdiv64(M, kRowsPerSplit), kMaxSplits) : 0; }
+
+// Rows per split: a multiple of the contraction step, at least kRowsPerSplit.
+static int64_t rows_per_split(int64_t M) {
+  const int64_t splits = gemm_tn_splits(M);
+  return ((cdiv64(M, splits) + kBK - 1) / kBK) * kBK;
+}
 
 cudaError_t launch_gemm_tn(const bf16 *G, int N1, const bf16 *X, int N2, int64_t M, float *part, cudaStream_t st) {
   const int64_t splits = gemm_tn_splits(M);
   if (splits == 0) return cudaSuccess;
   if (N2 % 64 != 0) return cudaErrorInvalidValue;
+  const int64_t rps = rows_per_split(M);
   if (N1 % 64 == 0) {
-    gemm_tn_kernel<64, 64><<<dim3(N2 / 64, N1 / 64, (unsigned)splits), 128, 0, st>>>(G, N1, X, N2, M, part);
+    gemm_tn_kernel<64, 64><<<dim3(N2 / 64, N1 / 64, (unsigned)splits), 128, 0, st>>>(G, N1, X, N2, M, rps, part);
   } else if (N1 % 32 == 0) {
-    gemm_tn_kernel<32, 64><<<dim3(N2 / 64, N1 / 32, (unsigned)splits), 128, 0, st>>>(G, N1, X, N2, M, part);
+    gemm_tn_kernel<32, 64><<<dim3(N2 / 64, N1 / 32, (unsigned)splits), 128, 0, st>>>(G, N1, X, N2, M, rps, part);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -599,7 +647,7 @@ cudaError_t launch_gemm_tn(const bf16 *G, int N1, const bf16 *X, int N2, int64_t
 cudaError_t launch_colsum(const bf16 *Y, int64_t M, int N, float *part, cudaStream_t st) {
   const int64_t chunks = gemm_tn_splits(M);
   if (chunks == 0) return cudaSuccess;
-  colsum_kernel<<<(unsigned)chunks, N, 0, st>>>(Y, M, N, part);
+  colsum_kernel<<<(unsigned)chunks, N, 0, st>>>(Y, M, N, rows_per_split(M), part);
   return cudaGetLastError();
 }
 
