@@ -109,8 +109,9 @@ enum {
 
 /* Kernel schedule of a PCG problem. */
 enum {
-  SSPCG_SCHED_AUTO = 0,     /* resident when the problem fits in one CTA's shared memory */
-  SSPCG_SCHED_RESIDENT = 1, /* operator and preconditioner staged once into shared memory */
+  SSPCG_SCHED_AUTO = 0,     /* as RESIDENT */
+  SSPCG_SCHED_RESIDENT = 1, /* operator and preconditioner staged once into shared memory (as many block
+                               rows as fit; the rest read from L2/HBM every iteration) */
   SSPCG_SCHED_STREAM = 2,   /* operator and preconditioner read from L2/HBM every iteration */
 };
 
