@@ -113,23 +113,35 @@ __device__ __forceinline__ double rcp_f64(double x) {
 __host__ __device__ __forceinline__ int inv_stride(int nx) { return (nx * (nx + 1) / 2) | 1; }
 __device__ __forceinline__ int tri(int i, int c) { return i * (i + 1) / 2 + c; }
 
-template <typename Real>
-__global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int2 *refs, int64_t total_knots,
-                                                         int nx, int kind, const Real *__restrict__ D, Real *PD,
-                                                         int32_t *status) {
+// D_k^-1 by FP64 LDL^T, G lanes per knot: the G lanes of a group share the
+// knot's packed triangle in shared memory and split the rows (LDL^T update,
+// D^-1 entries) or the columns (the triangular inverse) between them, so the
+// same shared memory holds G times more warps than one knot per thread.  All
+// knots of a launch have the same nx, so the lanes of a warp run the same
+// loops and synchronise with __syncwarp over the warp's active lanes.  Every
+// entry is computed with the same operations in the same order as one lane
+// would, so the result does not depend on G.
+template <typename Real, int G>
+__global__ void __launch_bounds__(512, 1) precond_inv_kernel(ProbSet ps, const int2 *refs, int64_t total_knots, int nx,
+                                                          int kind, const Real *__restrict__ D, Real *PD,
+                                                          int32_t *status) {
   extern __shared__ double dsm[];
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= total_knots) return;
+  const int lg = threadIdx.x % G, grp = threadIdx.x / G;
+  const int64_t g = (int64_t)blockIdx.x * (blockDim.x / G) + grp;
+  const bool active = g < total_knots;
+  const unsigned mask = __ballot_sync(0xffffffffu, active);
+  if (!active) return;
   const int2 ref = refs ? refs[g] : make_int2(0, (int)g);  // (problem, block row)
   const ProbDesc d = ps.get(ref.x);
   const int k = ref.y;
   const int nn = nx * nx;
   const Real *Dk = D + d.odiag + (int64_t)k * nn;
   Real *PDk = PD + d.odiag + (int64_t)k * nn;
-  if (kind == 3) {  // Jacobi
+  if (kind == 3) {  // Jacobi: reciprocal diagonal
     bool bad = false;
-    for (int e = 0; e < nn; ++e) PDk[e] = Real(0);
-    for (int i = 0; i < nx; ++i) {
+    for (int e = lg; e < nn; e += G) PDk[e] = Real(0);
+    __syncwarp(mask);
+    for (int i = lg; i < nx; i += G) {
       const Real s = Dk[i * nx + i];
       bad |= !(s > Real(0)) || !isfinite(s);
       PDk[i * nx + i] = Real(1) / s;
@@ -137,31 +149,33 @@ __global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int2
     if (bad) status[d.id] = kNotSpd;
     return;
   }
-  double *M = dsm + (int64_t)threadIdx.x * inv_stride(nx);
+  double *M = dsm + (int64_t)grp * (inv_stride(nx) + nx);
+  double *tmp = M + inv_stride(nx);
   for (int i = 0; i < nx; ++i)
-    for (int c = 0; c <= i; ++c) M[tri(i, c)] = (double)Dk[i * nx + c];
-  // LDL^T: after step j, M(j,j) = 1/d_j and M(i,j) = L(i,j) for i > j.
+    for (int c = lg; c <= i; c += G) M[tri(i, c)] = (double)Dk[i * nx + c];
+  __syncwarp(mask);
+  // LDL^T: after step j, M(j,j) = 1/d_j and M(i,j) = L(i,j) for i > j.  Rows i > j are split cyclically.
+  bool bad = false;
   for (int j = 0; j < nx; ++j) {
     const double djj = M[tri(j, j)];
-    if (!(djj > 0.0) || !isfinite(djj)) {
-      status[d.id] = kNotSpd;
-      for (int e = 0; e < nn; ++e) PDk[e] = Real(0);
-      return;
-    }
+    bad |= !(djj > 0.0) || !isfinite(djj);
     const double inv = rcp_f64(djj);
-    for (int i = nx - 1; i > j; --i) {
+    for (int i = j + 1 + lg; i < nx; i += G) {
       double *Mi = M + tri(i, 0);
       const double lij = Mi[j] * inv;
 #pragma unroll 4
       for (int c = j + 1; c <= i; ++c) Mi[c] = fma(-lij, M[tri(c, j)], Mi[c]);
-      Mi[j] = lij;
     }
-    M[tri(j, j)] = inv;
+    __syncwarp(mask);  // column j no longer read
+    for (int i = j + 1 + lg; i < nx; i += G) M[tri(i, j)] = M[tri(i, j)] * inv;
+    if (lg == 0) M[tri(j, j)] = inv;
+    __syncwarp(mask);
   }
-  // W = L^-1 (unit lower) in place, column by column.
-  for (int j = 0; j + 1 < nx; ++j) {
-    for (int i = j + 1; i < nx; ++i) {
-      const double *Mi = M + tri(i, 0);
+  // W = L^-1 (unit lower) in place, row by row; the columns of a row are split cyclically.
+  //   W(i,j) = -(L(i,j) + sum_{j<t<i} L(i,t) W(t,j))
+  for (int i = 1; i < nx; ++i) {
+    const double *Mi = M + tri(i, 0);
+    for (int j = lg; j < i; j += G) {
       double s0 = Mi[j], s1 = 0.0;  // two chains
       int t = j + 1;
       for (; t + 1 < i; t += 2) {
@@ -169,27 +183,38 @@ __global__ void __launch_bounds__(256) precond_inv_kernel(ProbSet ps, const int2
         s1 = fma(Mi[t + 1], M[tri(t + 1, j)], s1);
       }
       if (t < i) s0 = fma(Mi[t], M[tri(t, j)], s0);
-      M[tri(i, j)] = -(s0 + s1);
+      tmp[j] = -(s0 + s1);
     }
+    __syncwarp(mask);  // row i's L entries no longer read
+    for (int j = lg; j < i; j += G) M[tri(i, j)] = tmp[j];
+    __syncwarp(mask);
   }
-  // D^-1 = W^T diag(1/d) W, lower triangle, mirrored.
-  for (int i = 0; i < nx; ++i) {
-    for (int j = 0; j <= i; ++j) {
-      double s0 = M[tri(i, i)] * (i == j ? 1.0 : M[tri(i, j)]), s1 = 0.0;  // two chains
-      int t = i + 1;
-      for (; t + 1 < nx; t += 2) {
-        const double *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
-        s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
-        s1 = fma(Mu[i] * Mu[t + 1], Mu[j], s1);
-      }
-      if (t < nx) {
-        const double *Mt = M + tri(t, 0);
-        s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
-      }
-      const Real f = (Real)(s0 + s1);
-      PDk[i * nx + j] = f;
-      PDk[j * nx + i] = f;
+  if (bad) {
+    if (lg == 0) status[d.id] = kNotSpd;
+    for (int e = lg; e < nn; e += G) PDk[e] = Real(0);
+    return;
+  }
+  // D^-1 = W^T diag(1/d) W: lower-triangle entries split cyclically, mirrored.
+  const int npairs = nx * (nx + 1) / 2;
+  for (int e = lg; e < npairs; e += G) {
+    int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (tri(i + 1, 0) <= e) ++i;
+    while (tri(i, 0) > e) --i;
+    const int j = e - tri(i, 0);
+    double s0 = M[tri(i, i)] * (i == j ? 1.0 : M[tri(i, j)]), s1 = 0.0;  // two chains
+    int t = i + 1;
+    for (; t + 1 < nx; t += 2) {
+      const double *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
+      s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
+      s1 = fma(Mu[i] * Mu[t + 1], Mu[j], s1);
     }
+    if (t < nx) {
+      const double *Mt = M + tri(t, 0);
+      s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
+    }
+    const Real f = (Real)(s0 + s1);
+    PDk[i * nx + j] = f;
+    PDk[j * nx + i] = f;
   }
 }
 
@@ -278,20 +303,26 @@ cudaError_t launch_precond_inv(const ProbSet &ps, const int2 *refs, int64_t tota
                                const Real *D, Real *PD, int32_t *status, cudaStream_t st) {
   if (total_knots == 0) return cudaSuccess;
   static int attr_set = 0;
-  const int per_thread = inv_stride(nx) * (int)sizeof(double);
-  int threads = (int)std::min<int64_t>(256, (200 * 1024 / per_thread) / 32 * 32);
-  if (threads < 32) threads = 32;
-  if (kind == 3) threads = 256;
-  const size_t smem = kind == 3 ? 0 : (size_t)threads * per_thread;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(precond_inv_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(precond_inv_kernel<Real, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          210 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(precond_inv_kernel<Real, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = 1;
   }
-  const int64_t grid = cdiv(total_knots, threads);
-  precond_inv_kernel<Real><<<(unsigned)grid, threads, smem, st>>>(ps, refs, total_knots, nx, kind, D, PD,
-                                                                   status);
+  // lanes per knot: 8 for the larger blocks, 4 otherwise; knots per CTA limited by 200 KB of shared memory
+  const int G = nx >= 16 ? 8 : 4;
+  const int per_knot = (inv_stride(nx) + nx) * (int)sizeof(double);
+  int knots = (int)std::min<int64_t>(512 / G, (200 * 1024) / per_knot);
+  knots = std::max(32 / G, knots / (32 / G) * (32 / G));  // whole warps
+  const int threads = knots * G;
+  const size_t smem = kind == 3 ? 0 : (size_t)knots * per_knot;
+  const unsigned grid = (unsigned)cdiv(total_knots, knots);
+  if (G == 8)
+    precond_inv_kernel<Real, 8><<<grid, threads, smem, st>>>(ps, refs, total_knots, nx, kind, D, PD, status);
+  else
+    precond_inv_kernel<Real, 4><<<grid, threads, smem, st>>>(ps, refs, total_knots, nx, kind, D, PD, status);
   return cudaGetLastError();
 }
 
