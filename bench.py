@@ -60,6 +60,29 @@ def dist_init():
     return world, rank, local
 
 
+def rank_start(rank: int, per_rank: int) -> int:
+    """First problem index of a rank: every rank solves its own ``per_rank`` problems (weak scaling,
+    no data-path collective)."""
+    return rank * per_rank
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """The largest of the ranks' values (timings): the whole job's time is its slowest rank's."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job solves/s: all ranks' problems over the slowest rank's time."""
+    return world * per_rank * steps / (max_ms / 1e3)
+
+
 def workload_config(w, nprob):
     return {"workload": w.name, "problems_per_gpu": nprob, "N_range": list(w.N_range), "nx_set": list(w.nx_set),
             "nu_rule": "ceil(nx/2)", "h": w.h, "tol": w.tol, "precond": "symmetric stair",
@@ -204,7 +227,7 @@ def warm_start_comparison(args, torch, sspcg, stream, rank):
     torch.cuda.synchronize()
     train_s = time.time() - t0
     w = P.WARMSTART_EVAL_4096
-    probs = P.make_workload(w, count=w.nprob, start=rank * w.nprob)
+    probs = P.make_workload(w, count=w.nprob, start=rank_start(rank, w.nprob))
     plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
                                    sspcg.options(tol=w.tol))
     b = sspcg.Batch(plan, probs)
@@ -284,7 +307,7 @@ def main():
 
     w = WORKLOAD
     nprob = args.problems if args.problems > 0 else w.nprob
-    probs = P.make_workload(w, count=nprob, start=rank * nprob)  # weak scaling: each rank its own problems
+    probs = P.make_workload(w, count=nprob, start=rank_start(rank, nprob))  # weak scaling
     opts = sspcg.options(tol=w.tol)
     plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs], opts)
     b = sspcg.Batch(plan, probs, pin=True)
@@ -311,17 +334,13 @@ def main():
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
 
     iters = b.iters.cpu().numpy().astype(np.int64)
     status = b.status.cpu().numpy()
     relres = b.relres.cpu().numpy()
     ok = bool((status == 0).all() and (relres <= w.tol).all())
-    value = world * nprob * args.steps / (total_ms / 1e3)
+    value = job_throughput(world, nprob, args.steps, total_ms)
 
     # The pipeline overlaps one nx lane's build with the other lanes' solves, so the phases are timed
     # apart: the PCG launches alone (FP32, every problem, all groups concurrently) on the blocks the
@@ -376,11 +395,7 @@ def main():
                                       rr_h, st_h, stream)
         e1.record(stream)
         torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     h2d = sum(int(h[k].numel()) * 4 for k in ("A", "B", "qd", "rd", "gamma"))
     d2h = int(lam_h.numel()) * 4 + plan.nprob * (4 + 4 + 8)
 
@@ -403,7 +418,7 @@ def main():
                      "kernel": "pcg_kernel (all FP32 PCG launches of the batch, timed alone)",
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk "
                                     f"x {sm_max:.0f} MHz"},
-        "e2e": {"value": world * nprob * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_throughput(world, nprob, args.steps, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": None,
         "clocks": clk,
