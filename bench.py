@@ -34,6 +34,16 @@ WORKLOAD = P.RAGGED_BATCH_4096
 PRECOND = "sym"
 SMEM_BYTES_PER_CLK_PER_SM = 128  # shared-memory bandwidth of one SM (32 banks x 4 B per clock)
 MLP_FLOP_PER_ROW = 2 * (1344 * 256 + 256 * 256 + 256 * 32)  # warm-start network forward, one knot row
+def _hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json beside this file, else 6800 (fallback)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = _hbm_peak()
 MLP_MAX_ROWS = 1 << 19  # network workspace: the whole warm-start batch (266,240 knot rows) in one chunk
 
 
@@ -50,6 +60,9 @@ def parse():
     ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--train-problems", type=int, default=4096, help="training problems of the warm-start network")
     ap.add_argument("--train-epochs", type=int, default=6)
+    ap.add_argument("--mpc", action="store_true",
+                    help="add the MPC batch (16384 problems, 10 sequential re-solves, plain vs warm-started)")
+    ap.add_argument("--mpc-resolves", type=int, default=10)
     return ap.parse_args()
 
 
@@ -290,6 +303,72 @@ def warm_start_comparison(args, torch, sspcg, stream, rank):
             "gpu_launches": args.steps * (2 * launches_plain + 5 * chunks)}
 
 
+def mpc_comparison(args, torch, sspcg, stream, rank):
+    """MPC batch: 16384 problems (N ~ U{64..512}, nx ~ U{4..28}) whose gamma is perturbed by 1 % for each of
+    ``--mpc-resolves`` sequential re-solves.  Blocks and preconditioner are built once (A, B, Q, R do not
+    change); each re-solve is one PCG launch set, from lambda0 = 0 (plain) or from the previous solution
+    (warm, with fallback).  These problems do not fit in shared memory: the PCG streams its blocks from
+    HBM, so the roofline is the measured HBM copy bandwidth."""
+    import dataclasses
+    w = P.MPC_BATCH_16384
+    t0 = time.time()
+    probs = P.make_workload_parallel(w, count=w.nprob, start=rank_start(rank, w.nprob))
+    gen_s = time.time() - t0
+    plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
+                                   sspcg.options(tol=w.tol, warm_start=2))
+    b = sspcg.Batch(plan, probs)
+    d = b.dev
+    R = args.mpc_resolves
+    # gamma of re-solve 0 warms up (and starts the warm chain); re-solves 1..R are timed
+    gammas = [torch.from_numpy(plan.pack(sspcg.ARRAY_VEC, [P.perturb_gamma(p, r) for p in probs])).cuda()
+              for r in range(R + 1)]
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sspcg.sspcg_build_schur_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.D, b.E, stream)
+        sspcg.sspcg_build_precond_batched(plan, PRECOND, b.D, b.E, b.PD, b.PE, b.status, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+
+    def solve(g):
+        sspcg.sspcg_solve_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE, g, b.lam, b.iters, b.relres,
+                                     b.status, stream)
+
+    out = {}
+    for mode in ("plain", "warm"):
+        b.lam.zero_()
+        with torch.cuda.stream(stream):
+            solve(gammas[0])  # warm-up (also the start of the warm chain)
+        torch.cuda.synchronize()
+        iters, ok, alg = [], True, 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for r in range(1, R + 1):
+            if mode == "plain":
+                b.lam.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            solve(gammas[r])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            it = b.iters.cpu().numpy().astype(np.int64)
+            ok &= bool((b.status.cpu().numpy() == 0).all() and (b.relres.cpu().numpy() <= w.tol).all())
+            iters.append(float(it.mean()))
+            alg += sum(int(it[i]) * algorithmic_bytes_per_iteration(p) for i, p in enumerate(probs))
+        gbs = alg / (ms / 1e3) / 1e9
+        out[mode] = {"solves_per_s": len(probs) * R / (ms / 1e3), "ms_per_resolve": ms / R,
+                     "iters_mean_per_resolve": [round(x, 2) for x in iters], "all_converged": ok,
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                  "frac": gbs / HBM_PEAK_GBS, "peak_source": HBM_PEAK_SOURCE}}
+    stats = sspcg.plan_stats(plan)
+    return {"workload": w.name, "problems": len(probs), "resolves": R, "generate_seconds": round(gen_s, 1),
+            "build_ms": build_ms, "plain": out["plain"], "warm": out["warm"],
+            "speedup": out["warm"]["solves_per_s"] / out["plain"]["solves_per_s"],
+            "streamed_problems": stats["solve_qp_stream"], "pcg_launches_per_resolve": stats["solve_qp_launches"]}
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
@@ -433,6 +512,8 @@ def main():
     line["build_ms_per_step"] = build_ms
     if not args.no_warm_start:
         line["warm_start"] = warm_start_comparison(args, torch, sspcg, stream, rank)
+    if args.mpc:
+        line["mpc"] = mpc_comparison(args, torch, sspcg, stream, rank)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(probs, args.cpu_seconds, w.tol)
     print(json.dumps(line), flush=True)

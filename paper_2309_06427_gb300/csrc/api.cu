@@ -97,6 +97,9 @@ bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int *K, int64_t
   return true;
 }
 
+// Global-workspace slot (elements, a multiple of 4) of a problem whose vectors do not fit in shared memory.
+int64_t gvec_slot(int op, int N, int nx, int nu) { return round_up(pcg_layout(op, 0, N, nx, nu).total, 4); }
+
 sspcg_status validate_opts(const sspcg_options *o) {
   if (!o) return SSPCG_ERR_INVALID_ARG;
   if (!(o->tol >= 0.0)) return SSPCG_ERR_INVALID_ARG;
@@ -142,6 +145,8 @@ struct PcgGroup {
   int nx = 0;
   bool resident = false;
   bool f64 = false;
+  bool gvec = false;         // vectors in a global workspace (slot_elems per CTA from scratch_off)
+  int64_t slot_elems = 0, scratch_off = 0;
   int block = 0;
   int grid = 0;
   size_t smem = 0;
@@ -155,7 +160,8 @@ struct GroupSet {
   int op = kOpQp;
   bool f64 = false;
   std::vector<PcgGroup> groups;
-  int64_t n_resident = 0, n_stream = 0;
+  int64_t n_resident = 0, n_stream = 0, n_gvec = 0;
+  int64_t scratch_elems = 0;  // global workspace of its global-vector groups
 };
 
 enum { kSetQpAll = 0, kSetBlockAll = 1, kSetQpMain = 2, kSetTiny = 3, kNumSets = 4 };
@@ -192,6 +198,10 @@ struct sspcg_plan {
   int2 *d_tkref = nullptr, *d_toref = nullptr;
   int64_t tknots = 0, toff = 0, t_diag = 0, t_offe = 0;
   double *D64 = nullptr, *E64 = nullptr, *PD64 = nullptr, *PE64 = nullptr;
+  // global workspace of the global-vector groups (shared by the sets, which never run concurrently;
+  // the pipeline's FP32 and FP64 sets take disjoint parts)
+  void *d_scratch = nullptr;
+  int64_t tiny_scratch_byte_off = 0;  // the FP64 set's part in the pipeline
   // PCG launch groups
   int32_t *d_work = nullptr;
   int32_t *d_counters = nullptr;
@@ -222,7 +232,7 @@ void plan_free(sspcg_plan *p) {
   if (p->graph) cudaGraphExecDestroy(p->graph);
   for (void *ptr : {(void *)p->d_desc, (void *)p->d_kref, (void *)p->d_oref, (void *)p->d_knot_start, (void *)p->d_tdesc,
                     (void *)p->d_tkref, (void *)p->d_toref, (void *)p->D64, (void *)p->E64,
-                    (void *)p->PD64, (void *)p->PE64, (void *)p->d_work, (void *)p->d_counters, (void *)p->hbuf,
+                    (void *)p->PD64, (void *)p->PE64, (void *)p->d_work, (void *)p->d_counters, (void *)p->d_scratch, (void *)p->hbuf,
                     (void *)p->hint, (void *)p->hdbl})
     cudaFree(ptr);
   for (auto *v : {&p->nxg_all, &p->nxg_tiny})
@@ -246,14 +256,19 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
                          const std::vector<int32_t> &members, std::vector<int32_t> &work_host, int32_t &pos) {
   // class 0: not fully resident (takes the whole budget); classes 1..3: fully resident within
   // budget/2, /4, /8 (several CTAs per SM); class 4: the rest of the fully resident problems
-  constexpr int kClasses = 5;
+  // class 5: vectors in a global workspace (they alone exceed the shared memory)
+  constexpr int kClasses = 6;
   std::vector<std::vector<int32_t>> buckets(kClasses * (kMaxNx + 1));
   std::vector<int64_t> bytes(descs.size(), 0);
   const int64_t budget = smem_budget();
   for (int32_t i : members) {
     const ProbDesc &d = descs[i];
     int K = 0;
-    if (!pcg_fit(set.op, p->opts.schedule, d.N, d.nx, d.nu, set.f64, &K, &bytes[i])) return SSPCG_ERR_UNSUPPORTED;
+    if (!pcg_fit(set.op, p->opts.schedule, d.N, d.nx, d.nu, set.f64, &K, &bytes[i])) {
+      bytes[i] = gvec_slot(set.op, d.N, d.nx, d.nu);  // slot elements
+      buckets[kClasses * d.nx + 5].push_back(i);
+      continue;
+    }
     int cls = 0;
     if (K == d.N + 1) {
       const int64_t need = bytes[i] + kPcgStaticSmem + 1024;
@@ -268,7 +283,8 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
       std::stable_sort(b.begin(), b.end(), [&](int32_t x, int32_t y) { return descs[x].N > descs[y].N; });
       PcgGroup g;
       g.nx = nx;
-      g.resident = r != 0;
+      g.resident = r != 0 && r != 5;
+      g.gvec = r == 5;
       g.f64 = set.f64;
       int64_t maxrows = 0, maxsmem = 0;
       for (int32_t i : b) {
@@ -277,16 +293,25 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
         maxsmem = std::max<int64_t>(maxsmem, bytes[i]);
       }
       g.block = p->opts.block_threads > 0 ? p->opts.block_threads : auto_block(maxrows);
-      g.smem = (size_t)maxsmem;
-      const int64_t per_sm_smem = 228 * 1024;
-      const int by_smem = (int)std::max<int64_t>(1, per_sm_smem / (maxsmem + kPcgStaticSmem + 1024));
       const int by_thr = std::max(1, 2048 / g.block);
-      g.grid = (int)std::min<int64_t>((int64_t)b.size(), (int64_t)std::min(by_smem, by_thr) * device_sms());
+      if (g.gvec) {
+        // two CTAs per SM at most: each holds a workspace slot (about 7 (N+1) nx values)
+        g.smem = 0;
+        g.slot_elems = maxsmem;
+        g.grid = (int)std::min<int64_t>((int64_t)b.size(), (int64_t)std::min(2, by_thr) * device_sms());
+        g.scratch_off = set.scratch_elems;
+        set.scratch_elems += (int64_t)g.grid * g.slot_elems;
+      } else {
+        g.smem = (size_t)maxsmem;
+        const int64_t per_sm_smem = 228 * 1024;
+        const int by_smem = (int)std::max<int64_t>(1, per_sm_smem / (maxsmem + kPcgStaticSmem + 1024));
+        g.grid = (int)std::min<int64_t>((int64_t)b.size(), (int64_t)std::min(by_smem, by_thr) * device_sms());
+      }
       g.nwork = (int32_t)b.size();
       g.d_work = p->d_work + pos;
       g.counter_index = p->ngroups_total++;
       for (int32_t i : b) work_host[pos++] = i;
-      (g.resident ? set.n_resident : set.n_stream) += g.nwork;
+      (g.gvec ? set.n_gvec : g.resident ? set.n_resident : set.n_stream) += g.nwork;
       set.groups.push_back(g);
     }
   }
@@ -308,17 +333,29 @@ struct SetLaunch {
   PcgArgs args;
 };
 
+// Vectors of a global-vector group: its part of the plan's workspace (the FP64 set of the pipeline sits
+// after the FP32 set's part).
+void set_gvec(PcgArgs &a, const sspcg_plan *p, const GroupSet &set, const PcgGroup &g) {
+  a.gscratch = nullptr;
+  a.gstride = 0;
+  if (!g.gvec || !p->d_scratch) return;
+  char *base = static_cast<char *>(p->d_scratch);
+  if (&set == &p->sets[kSetTiny]) base += p->tiny_scratch_byte_off;
+  a.gscratch = base + g.scratch_off * (set.f64 ? sizeof(double) : sizeof(float));
+  a.gstride = g.slot_elems;
+}
+
 // Launch the groups of several sets concurrently: fork side streams off
 // ``st``, one group per stream, join back.
 sspcg_status launch_sets(sspcg_plan *p, std::initializer_list<SetLaunch> list, cudaStream_t st) {
   struct Item {
     const PcgGroup *g;
     const PcgArgs *a;
-    int op;
+    const GroupSet *set;
   };
   std::vector<Item> all;
   for (const SetLaunch &sl : list)
-    for (const PcgGroup &g : sl.set->groups) all.push_back({&g, &sl.args, sl.set->op});
+    for (const PcgGroup &g : sl.set->groups) all.push_back({&g, &sl.args, sl.set});
   if (all.empty()) return SSPCG_OK;
   SSPCG_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int32_t) * p->ngroups_total, st));
   const size_t ng = all.size();
@@ -332,9 +369,10 @@ sspcg_status launch_sets(sspcg_plan *p, std::initializer_list<SetLaunch> list, c
     a.work = g.d_work;
     a.nwork = g.nwork;
     a.counter = p->d_counters + g.counter_index;
+    set_gvec(a, p, *all[i].set, g);
     cudaStream_t s = i == 0 ? st : p->side[i - 1];
     const int red = g.f64 ? kRedF64 : red_mode(p->opts.reduction);
-    SSPCG_CUDA(launch_pcg(g.nx, all[i].op, red, g.f64, a, g.grid, g.block, g.smem, s));
+    SSPCG_CUDA(launch_pcg(g.nx, all[i].set->op, red, g.f64, a, g.grid, g.block, g.smem, s));
   }
   for (size_t i = 1; i < ng; ++i) {
     SSPCG_CUDA(cudaEventRecord(p->ev[i], p->side[i - 1]));
@@ -601,6 +639,15 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     if ((s = plan_groups(p, p->sets[kSetTiny], p->tdesc, tiny_local, work, pos)) != SSPCG_OK) return fail(s);
     if ((e = cudaMemcpy(p->d_work, work.data(), sizeof(int32_t) * nwork, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e));
+    {
+      // bytes: the largest set alone, or the pipeline's FP32 and FP64 sets side by side
+      const int64_t b32 = (int64_t)sizeof(float), b64 = (int64_t)sizeof(double);
+      auto sb = [&](int k) { return p->sets[k].scratch_elems * (p->sets[k].f64 ? b64 : b32); };
+      const int64_t main_bytes = round_up(sb(kSetQpMain), 64);
+      int64_t need = std::max({sb(kSetQpAll), sb(kSetBlockAll), main_bytes + sb(kSetTiny)});
+      p->tiny_scratch_byte_off = main_bytes;
+      if (need > 0 && (e = cudaMalloc(&p->d_scratch, need)) != cudaSuccess) return fail(cuda_fail(e));
+    }
     if ((e = cudaMalloc(&p->d_counters, sizeof(int32_t) * std::max(1, p->ngroups_total))) != cudaSuccess)
       return fail(cuda_fail(e));
     size_t nside = 0;
@@ -647,12 +694,12 @@ sspcg_status sspcg_plan_stats(const sspcg_plan *plan, int64_t *out) {
   const GroupSet &m = plan->sets[kSetQpMain], &t = plan->sets[kSetTiny];
   out[0] = (int64_t)(m.groups.size() + t.groups.size());
   out[1] = m.n_resident;
-  out[2] = m.n_stream;
+  out[2] = m.n_stream + m.n_gvec;
   out[3] = plan->ntiny;
   out[4] = (int64_t)plan->sets[kSetQpAll].groups.size();
   out[5] = (int64_t)plan->sets[kSetBlockAll].groups.size();
   out[6] = plan->sets[kSetQpAll].n_resident;
-  out[7] = plan->sets[kSetQpAll].n_stream;
+  out[7] = plan->sets[kSetQpAll].n_stream + plan->sets[kSetQpAll].n_gvec;
   return SSPCG_OK;
 }
 
@@ -857,6 +904,7 @@ static sspcg_status pipeline_lanes(sspcg_plan *p, sspcg_precond kind, const floa
       a.work = g.d_work;
       a.nwork = g.nwork;
       a.counter = p->d_counters + g.counter_index;
+      set_gvec(a, p, set, g);
       const int red = g.f64 ? kRedF64 : red_mode(p->opts.reduction);
       SSPCG_CUDA(launch_pcg(g.nx, set.op, red, g.f64, a, g.grid, g.block, g.smem, s));
       if (!first) {

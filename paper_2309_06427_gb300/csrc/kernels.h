@@ -96,6 +96,8 @@ struct PcgArgs {
   int32_t warm;          // 0, 1, 2 (see sspcg_options)
   int64_t smem_elems;    // dynamic shared memory of the launch, in elements of the working precision
   int32_t max_resident;  // cap on staged block rows (a schedule override); large = no cap
+  void *gscratch;        // vectors in global memory: CTA b uses gscratch + b * gstride elements
+  int64_t gstride;       //   (nullptr: vectors in shared memory)
 };
 
 // PCG launch for one nx; dispatches to the instantiation for that nx.

@@ -19,7 +19,8 @@
 //
 // The first K block rows of the operator and preconditioner blocks are
 // staged in shared memory (odd row strides); the rest are read from global
-// memory every iteration (L1/L2).
+// memory every iteration (L1/L2).  Problems whose vectors alone exceed the
+// shared memory keep them in a per-CTA slot of a global workspace (K = 0).
 //
 // Real is the working precision (float: the fast path; double: the FP64
 // path).  The QP data A, B, diag Q, diag R and gamma are FP32 inputs in both
@@ -459,7 +460,9 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
 template <int NX, int OP, int RED, typename Real>
 __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
   extern __shared__ float4 smem4[];
-  Real *sm = reinterpret_cast<Real *>(smem4);
+  // vectors in shared memory, or in this CTA's slot of a global workspace when they do not fit
+  Real *sm = a.gscratch ? reinterpret_cast<Real *>(a.gscratch) + (int64_t)blockIdx.x * a.gstride
+                        : reinterpret_cast<Real *>(smem4);
   __shared__ __align__(16) typename Red<RED, Real>::T slots[4 * 32];
   __shared__ int s_next;
   int stride_i = 0;

@@ -218,3 +218,27 @@ def mlp_initial_params(seed: int = 0) -> np.ndarray:
     w2 = (2.0 * u[n1:] - 1.0) / math.sqrt(256)
     parts = [w1, np.zeros(256), w2, np.zeros(256), np.zeros(32 * 256), np.zeros(32)]
     return np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)
+
+
+def _chunk(args):
+    config, count, start = args
+    return make_workload(WORKLOADS[config], count=count, start=start)
+
+
+def make_workload_parallel(w: Workload, count: int | None = None, start: int = 0, workers: int | None = None,
+                           chunk: int = 256) -> List[Problem]:
+    """``make_workload`` split over a pool of spawned processes (the same problems, in order).  Spawned, not
+    forked, so that it is safe after the parent has initialised CUDA."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    count = w.nprob - start if count is None else count
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers <= 1 or count <= chunk:
+        return make_workload(w, count, start)
+    jobs = [(w.config, min(chunk, count - i), start + i) for i in range(0, count, chunk)]
+    out: List[Problem] = []
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        for part in ex.map(_chunk, jobs):
+            out.extend(part)
+    return out

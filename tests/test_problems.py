@@ -47,3 +47,14 @@ def test_gamma_perturbation_is_one_percent():
     rel = (g1 / p.gamma - 1)
     assert 0.005 < rel.std() < 0.015
     assert not np.array_equal(g1, P.perturb_gamma(p, 1))
+
+
+def test_parallel_generation_matches_serial():
+    from paper_2309_06427_gb300 import problems as P
+    a = P.make_workload(P.MPC_BATCH_16384, count=20, start=100)
+    b = P.make_workload_parallel(P.MPC_BATCH_16384, count=20, start=100, workers=2, chunk=7)
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        assert x.key == y.key and x.N == y.N and x.nx == y.nx
+        for f in ("A", "B", "qd", "rd", "gamma"):
+            assert np.array_equal(getattr(x, f), getattr(y, f))
