@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--mpc", action="store_true",
                     help="add the MPC batch (16384 problems, 10 sequential re-solves, plain vs warm-started)")
     ap.add_argument("--mpc-resolves", type=int, default=10)
+    ap.add_argument("--mpc-problems", type=int, default=0, help="first N problems of the MPC batch; 0: all")
     return ap.parse_args()
 
 
@@ -312,7 +313,8 @@ def mpc_comparison(args, torch, sspcg, stream, rank):
     import dataclasses
     w = P.MPC_BATCH_16384
     t0 = time.time()
-    probs = P.make_workload_parallel(w, count=w.nprob, start=rank_start(rank, w.nprob))
+    count = args.mpc_problems if args.mpc_problems > 0 else w.nprob
+    probs = P.make_workload_parallel(w, count=count, start=rank_start(rank, count))
     gen_s = time.time() - t0
     plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
                                    sspcg.options(tol=w.tol, warm_start=2))
