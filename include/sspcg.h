@@ -270,7 +270,9 @@ sspcg_status sspcg_build_schur_batched(sspcg_plan *plan, const float *A, const f
 sspcg_status sspcg_build_precond_batched(sspcg_plan *plan, sspcg_precond kind, const float *D, const float *E,
                                          float *PD, float *PE, int32_t *status, sspcg_stream stream);
 
-/* Batched sspcg_solve (block S). iters, status: int32[nprob]; relres: double[nprob]. */
+/* Batched sspcg_solve (block S). iters, status: int32[nprob]; relres: double[nprob].
+ * SSPCG_ERR_UNSUPPORTED when a problem's PCG vectors (about 7 (N+1) nx values) exceed one CTA's shared
+ * memory: the block form has no global-workspace kernels (the QP-form calls do). */
 sspcg_status sspcg_solve_batched(sspcg_plan *plan, const float *D, const float *E, const float *PD,
                                  const float *PE, const float *gamma, float *lambda, int32_t *iters,
                                  double *relres, int32_t *status, sspcg_stream stream);

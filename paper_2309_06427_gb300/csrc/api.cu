@@ -162,6 +162,7 @@ struct GroupSet {
   std::vector<PcgGroup> groups;
   int64_t n_resident = 0, n_stream = 0, n_gvec = 0;
   int64_t scratch_elems = 0;  // global workspace of its global-vector groups
+  bool unsupported = false;   // holds problems that this set's operator form cannot solve
 };
 
 enum { kSetQpAll = 0, kSetBlockAll = 1, kSetQpMain = 2, kSetTiny = 3, kNumSets = 4 };
@@ -265,6 +266,10 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
     const ProbDesc &d = descs[i];
     int K = 0;
     if (!pcg_fit(set.op, p->opts.schedule, d.N, d.nx, d.nu, set.f64, &K, &bytes[i])) {
+      if (set.op != kOpQp) {  // global-vector kernels exist for the QP operator form only
+        set.unsupported = true;
+        continue;
+      }
       bytes[i] = gvec_slot(set.op, d.N, d.nx, d.nu);  // slot elements
       buckets[kClasses * d.nx + 5].push_back(i);
       continue;
@@ -778,6 +783,7 @@ sspcg_status sspcg_solve_batched(sspcg_plan *plan, const float *D, const float *
   sspcg_status s = check_solve_args(plan, kOpBlock, nullptr, nullptr, nullptr, nullptr, D, E, PD, PE, gamma, lambda,
                                     iters, relres, status);
   if (s != SSPCG_OK) return s;
+  if (plan->sets[kSetBlockAll].unsupported) return SSPCG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
   plan->build_timed = false;

@@ -457,12 +457,14 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
 
 // Persistent kernel: CTAs take problems from the work list, through an
 // atomic counter when one is given (largest problems first), else by stride.
-template <int NX, int OP, int RED, typename Real>
+// GV: vectors in this CTA's slot of a global workspace (problems whose vectors do not fit in shared
+// memory).  A compile-time choice, so that the other launches address their vectors as shared memory.
+template <int NX, int OP, int RED, typename Real, bool GV>
 __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
   extern __shared__ float4 smem4[];
-  // vectors in shared memory, or in this CTA's slot of a global workspace when they do not fit
-  Real *sm = a.gscratch ? reinterpret_cast<Real *>(a.gscratch) + (int64_t)blockIdx.x * a.gstride
-                        : reinterpret_cast<Real *>(smem4);
+  Real *sm;
+  if constexpr (GV) sm = reinterpret_cast<Real *>(a.gscratch) + (int64_t)blockIdx.x * a.gstride;
+  else sm = reinterpret_cast<Real *>(smem4);
   __shared__ __align__(16) typename Red<RED, Real>::T slots[4 * 32];
   __shared__ int s_next;
   int stride_i = 0;
@@ -484,9 +486,9 @@ __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
   }
 }
 
-template <int NX, int OP, int RED, typename Real>
+template <int NX, int OP, int RED, typename Real, bool GV>
 cudaError_t launch_variant(const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
-  auto k = pcg_kernel<NX, OP, RED, Real>;
+  auto k = pcg_kernel<NX, OP, RED, Real, GV>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_max_smem_bytes());
@@ -500,16 +502,25 @@ cudaError_t launch_variant(const PcgArgs &a, int grid, int block, size_t smem, c
 }
 
 // All variants of one nx: FP32 with three reduction modes for both operator
-// forms, and the FP64 path (QP form, FP64 reductions).
+// forms, and the FP64 path (QP form, FP64 reductions); vectors in a global
+// workspace for the QP form only.
 template <int NX>
 cudaError_t launch_pcg_for_nx(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
                               cudaStream_t st) {
+  if (a.gscratch) {
+    if (op != kOpQp) return cudaErrorInvalidValue;
+    if (f64) return launch_variant<NX, kOpQp, kRedF64, double, true>(a, grid, block, smem, st);
+    if (red == kRedDf) return launch_variant<NX, kOpQp, kRedDf, float, true>(a, grid, block, smem, st);
+    if (red == kRedF32) return launch_variant<NX, kOpQp, kRedF32, float, true>(a, grid, block, smem, st);
+    if (red == kRedF64) return launch_variant<NX, kOpQp, kRedF64, float, true>(a, grid, block, smem, st);
+    return cudaErrorInvalidValue;
+  }
   if (f64) {
     if (op != kOpQp) return cudaErrorInvalidValue;
-    return launch_variant<NX, kOpQp, kRedF64, double>(a, grid, block, smem, st);
+    return launch_variant<NX, kOpQp, kRedF64, double, false>(a, grid, block, smem, st);
   }
 #define SSPCG_PCG_CASE(OPV, REDV) \
-  if (op == OPV && red == REDV) return launch_variant<NX, OPV, REDV, float>(a, grid, block, smem, st);
+  if (op == OPV && red == REDV) return launch_variant<NX, OPV, REDV, float, false>(a, grid, block, smem, st);
   SSPCG_PCG_CASE(kOpQp, kRedDf)
   SSPCG_PCG_CASE(kOpQp, kRedF32)
   SSPCG_PCG_CASE(kOpQp, kRedF64)
