@@ -113,7 +113,7 @@ __device__ __forceinline__ double rcp_f64(double x) {
 __host__ __device__ __forceinline__ int inv_stride(int nx) { return (nx * (nx + 1) / 2) | 1; }
 __device__ __forceinline__ int tri(int i, int c) { return i * (i + 1) / 2 + c; }
 
-// D_k^-1 by FP64 LDL^T, G lanes per knot: the G lanes of a group share the
+// D_k^-1 by FP64 LDL^T and D^-1 = V^T V with V = diag(1/d)^(1/2) L^-1, G lanes per knot: the G lanes of a group share the
 // knot's packed triangle in shared memory and split the rows (LDL^T update,
 // D^-1 entries) or the columns (the triangular inverse) between them, so the
 // same shared memory holds G times more warps than one knot per thread.  All
@@ -189,28 +189,55 @@ __global__ void __launch_bounds__(512, 1) precond_inv_kernel(ProbSet ps, const i
     for (int j = lg; j < i; j += G) M[tri(i, j)] = tmp[j];
     __syncwarp(mask);
   }
+  // FP32 output: V = diag(1/d)^(1/2) W (row t of W scaled by sqrt(1/d_t); V(t,t) = sqrt(1/d_t)), so that
+  // D^-1 = W^T diag(1/d) W = V^T V costs one FMA per term.  Rows split cyclically.  FP64 output keeps
+  // W^T diag(1/d) W term by term (two operations per term, the rounding the FP64 path is checked with).
+  constexpr bool kVtV = sizeof(Real) == sizeof(float);
+  if (kVtV && !bad) {
+    for (int t = lg; t < nx; t += G) {
+      double *Mt = M + tri(t, 0);
+      const double sc = sqrt(Mt[t]);
+      for (int c = 0; c < t; ++c) Mt[c] *= sc;
+      Mt[t] = sc;
+    }
+  }
+  __syncwarp(mask);  // the last synchronisation: groups may leave from here on
   if (bad) {
     if (lg == 0) status[d.id] = kNotSpd;
     for (int e = lg; e < nn; e += G) PDk[e] = Real(0);
     return;
   }
-  // D^-1 = W^T diag(1/d) W: lower-triangle entries split cyclically, mirrored.
+  // D^-1(i,j): lower-triangle entries split cyclically, mirrored.
   const int npairs = nx * (nx + 1) / 2;
   for (int e = lg; e < npairs; e += G) {
     int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
     while (tri(i + 1, 0) <= e) ++i;
     while (tri(i, 0) > e) --i;
     const int j = e - tri(i, 0);
-    double s0 = M[tri(i, i)] * (i == j ? 1.0 : M[tri(i, j)]), s1 = 0.0;  // two chains
+    double s0, s1 = 0.0;  // two chains
     int t = i + 1;
-    for (; t + 1 < nx; t += 2) {
-      const double *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
-      s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
-      s1 = fma(Mu[i] * Mu[t + 1], Mu[j], s1);
-    }
-    if (t < nx) {
-      const double *Mt = M + tri(t, 0);
-      s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
+    if constexpr (kVtV) {
+      s0 = M[tri(i, i)] * M[tri(i, j)];
+      for (; t + 1 < nx; t += 2) {
+        const double *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
+        s0 = fma(Mt[i], Mt[j], s0);
+        s1 = fma(Mu[i], Mu[j], s1);
+      }
+      if (t < nx) {
+        const double *Mt = M + tri(t, 0);
+        s0 = fma(Mt[i], Mt[j], s0);
+      }
+    } else {
+      s0 = M[tri(i, i)] * (i == j ? 1.0 : M[tri(i, j)]);
+      for (; t + 1 < nx; t += 2) {
+        const double *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
+        s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
+        s1 = fma(Mu[i] * Mu[t + 1], Mu[j], s1);
+      }
+      if (t < nx) {
+        const double *Mt = M + tri(t, 0);
+        s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
+      }
     }
     const Real f = (Real)(s0 + s1);
     PDk[i * nx + j] = f;
