@@ -34,6 +34,25 @@ WORKLOAD = P.RAGGED_BATCH_4096
 PRECOND = "sym"
 SMEM_BYTES_PER_CLK_PER_SM = 128  # shared-memory bandwidth of one SM (32 banks x 4 B per clock)
 MLP_FLOP_PER_ROW = 2 * (1344 * 256 + 256 * 256 + 256 * 32)  # warm-start network forward, one knot row
+def pcg_traffic():
+    """DRAM bytes of one PCG-only solve of the benchmark batch, from the committed ncu launch-list summary,
+    if the kernel and planner sources are unchanged since it was captured; else None."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", "launches_ragged4096_pipeline.md")).read()
+        vals = dict(line.split(":", 1) for line in text.splitlines()
+                    if line.startswith(("pcg_traffic_bytes_per_solve:", "source_sha256_16:")))
+        h = hashlib.sha256()
+        for f in ("pcg.cuh", "api.cu"):
+            with open(os.path.join(ROOT, "paper_2309_06427_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] != vals["source_sha256_16"].strip():
+            return None
+        return int(vals["pcg_traffic_bytes_per_solve"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _hbm_peak():
     """Measured HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json beside this file, else 6800 (fallback)."""
     try:
@@ -495,7 +514,11 @@ def main():
         "all_converged": ok,
         "pcg_ms_per_step": pcg_ms,
         "roofline": {"bound": "smem", "achieved": achieved_gbs, "peak": smem_peak_gbs, "unit": "GB/s",
-                     "frac": achieved_gbs / smem_peak_gbs, "traffic": None,
+                     "frac": achieved_gbs / smem_peak_gbs,
+                     "traffic": pcg_traffic() if nprob == w.nprob else None,
+                     "traffic_note": "DRAM bytes per PCG-only solve of the batch (ncu, profiles/); the blocks are "
+                                     "read from shared memory and L2, so HBM traffic is far below the "
+                                     "algorithmic bytes",
                      "kernel": "pcg_kernel (all FP32 PCG launches of the batch, timed alone)",
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk "
                                     f"x {sm_max:.0f} MHz"},
