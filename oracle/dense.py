@@ -16,6 +16,10 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   Sec. IV (symmetric stair), Sec. III (additive stair), Eq. (jacobi).
 * ``cholesky_solve``: the exact solution of S x = gamma.
 * ``pcg``: textbook PCG on dense matrices (Saad, Alg. 9.1).
+* ``form_gamma``, ``recover_step``: the two outer steps of Eq. (schur), written
+  densely: gamma = c - C G^-1 g and delta z = G^-1 (g - C^T lambda*), with the
+  paper's lambda* = -mu (mu solves C G^-1 C^T mu = gamma).  ``kkt_solve``: the
+  same QP step by one dense solve of the whole KKT system.
 """
 from __future__ import annotations
 
@@ -133,3 +137,61 @@ def spectrum(Minv, S) -> np.ndarray:
 def condition_number(Minv, S) -> float:
     ev, _ = spectrum(Minv, S)
     return ev[-1] / ev[0]
+
+
+def _z_vector(q, r):
+    """Stack state and input vectors in the variable order of ``kkt`` (x_0, u_0, ..., x_N)."""
+    q, r = np.asarray(q, dtype=np.float64), np.asarray(r, dtype=np.float64)
+    N = q.shape[0] - 1
+    parts = []
+    for k in range(N + 1):
+        parts.append(q[k])
+        if k < N:
+            parts.append(r[k])
+    return np.concatenate(parts) if parts else np.zeros(0)
+
+
+def _split_z(z, N, nx, nu):
+    dx = np.zeros((N + 1, nx)); du = np.zeros((N, nu))
+    o = 0
+    for k in range(N + 1):
+        dx[k] = z[o:o + nx]; o += nx
+        if k < N:
+            du[k] = z[o:o + nu]; o += nu
+    return dx, du
+
+
+def form_gamma(A, B, qd, rd, c, q, r) -> np.ndarray:
+    """gamma = c - C G^-1 g (Eq. schur), g = (q_0, r_0, ..., q_N); returned as [N+1, nx]."""
+    G, C = kkt(A, B, qd, rd)
+    g = _z_vector(q, r)
+    c = np.asarray(c, dtype=np.float64)
+    return (c.ravel() - C @ np.linalg.solve(G, g)).reshape(c.shape)
+
+
+def recover_step(A, B, qd, rd, q, r, mu):
+    """delta z = G^-1 (g - C^T lambda*) with lambda* = -mu (Eq. schur): (dx [N+1, nx], du [N, nu])."""
+    G, C = kkt(A, B, qd, rd)
+    g = _z_vector(q, r)
+    lam = -np.asarray(mu, dtype=np.float64).ravel()
+    z = np.linalg.solve(G, g - C.T @ lam)
+    qd = np.asarray(qd)
+    N, nx = qd.shape[0] - 1, qd.shape[1]
+    nu = np.asarray(r).shape[1] if N > 0 else 0
+    return _split_z(z, N, nx, nu)
+
+
+def kkt_solve(A, B, qd, rd, c, q, r):
+    """The QP step from one dense solve of [[G, C^T], [C, 0]] [z; lambda] = [g; c] (the KKT system of
+    minimising z^T G z / 2 - g^T z subject to C z = c): (dx, du, lambda [N+1, nx])."""
+    G, C = kkt(A, B, qd, rd)
+    g = _z_vector(q, r)
+    nz, nc = G.shape[0], C.shape[0]
+    K = np.block([[G, C.T], [C, np.zeros((nc, nc))]])
+    sol = np.linalg.solve(K, np.concatenate([g, np.asarray(c, dtype=np.float64).ravel()]))
+    qd = np.asarray(qd)
+    N, nx = qd.shape[0] - 1, qd.shape[1]
+    nu = np.asarray(r).shape[1] if N > 0 else 0
+    dx, du = _split_z(sol[:nz], N, nx, nu)
+    return dx, du, sol[nz:].reshape(N + 1, nx)
+

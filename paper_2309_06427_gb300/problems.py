@@ -242,3 +242,13 @@ def make_workload_parallel(w: Workload, count: int | None = None, start: int = 0
         for part in ex.map(_chunk, jobs):
             out.extend(part)
     return out
+
+
+def qp_vectors(p: Problem, seed: int = 0):
+    """Constraint values c [N+1, nx] and cost gradients q [N+1, nx], r [N, nu] of problem ``p`` (FP32),
+    N(0, 1) entries from stream ``p.key + (seed + 1) * 2**56`` in the order c, q, r."""
+    n, m, u = p.N + 1, p.nx, p.nu
+    z = normals(p.key + ((seed + 1) << 56), 2 * n * m + p.N * u, 0)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return (f32(z[:n * m].reshape(n, m)), f32(z[n * m:2 * n * m].reshape(n, m)),
+            f32(z[2 * n * m:].reshape(p.N, u)))
