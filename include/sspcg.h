@@ -465,6 +465,37 @@ sspcg_status sspcg_pipeline_warm_batched(sspcg_plan *plan, sspcg_mlp *mlp, sspcg
                                          float *D, float *E, float *PD, float *PE, float *lambda, int32_t *iters,
                                          double *relres, int32_t *status, sspcg_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* The QP step around the solve (Eq. schur)                           */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper's Eq. (schur) is self-consistent for the QP of minimising
+ * z^T G z / 2 - g^T z subject to C z = c, whose step is found by
+ *   gamma = c - C G^-1 g,  S lambda* = gamma (S = -C G^-1 C^T),  delta z = G^-1 (g - C^T lambda*).
+ * The library solves (C G^-1 C^T) mu = gamma, mu = -lambda* (see the sign note above), so
+ *   delta z = G^-1 (g + C^T mu).
+ * g = (q_0, r_0, q_1, ..., q_N) is the cost gradient; c [N+1][nx] holds the
+ * constraint values (row 0: initial state, row k+1: dynamics defect of knot k).
+ * In the block notation of Sec. II-A (zeta_k = A_k Q_k^-1 q_k + B_k R_k^-1 r_k - Q_{k+1}^-1 q_{k+1}):
+ *   gamma_0 = c_0 + Q_0^-1 q_0,  gamma_{k+1} = c_{k+1} - zeta_k.
+ * (The paper's block listing writes c + zeta_k; Eq. (schur)'s sign is used.)
+ * Layouts: c, q, gamma, mu, dx like gamma ([N+1][nx]); r, du like diag R ([N][nu]).
+ * FP32 in and out; one pass over A and B.
+ */
+sspcg_status sspcg_form_gamma(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
+                              const float *rd, const float *c, const float *q, const float *r, float *gamma,
+                              sspcg_stream stream);
+sspcg_status sspcg_recover_step(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *qd,
+                                const float *rd, const float *q, const float *r, const float *mu, float *dx,
+                                float *du, sspcg_stream stream);
+/* The same over a plan's packed arrays (c, q, gamma, mu, dx: SSPCG_ARRAY_VEC; r, du: SSPCG_ARRAY_RD). */
+sspcg_status sspcg_form_gamma_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
+                                      const float *rd, const float *c, const float *q, const float *r, float *gamma,
+                                      sspcg_stream stream);
+sspcg_status sspcg_recover_step_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
+                                        const float *rd, const float *q, const float *r, const float *mu, float *dx,
+                                        float *du, sspcg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

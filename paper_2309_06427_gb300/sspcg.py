@@ -111,6 +111,10 @@ def lib() -> ctypes.CDLL:
             "sspcg_mlp_infer": [_VP] * 10,
             "sspcg_mlp_train_step": [_VP, _VP, _I32, _I32] + [_VP] * 9 + [ctypes.POINTER(Adam), _VP, _VP],
             "sspcg_pipeline_warm_batched": [_VP, _VP, _I32] + [_VP] * 14,
+            "sspcg_form_gamma": [_I32, _I32, _I32] + [_VP] * 9,
+            "sspcg_recover_step": [_I32, _I32, _I32] + [_VP] * 10,
+            "sspcg_form_gamma_batched": [_VP] * 10,
+            "sspcg_recover_step_batched": [_VP] * 11,
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -348,6 +352,30 @@ def sspcg_solve_qp_batched_noalloc(N, nx, nu, A, B, qd, rd, PD, PE, gamma, lam, 
                                                 _ptr(B), _ptr(qd), _ptr(rd), _ptr(PD), _ptr(PE), _ptr(gamma),
                                                 _ptr(lam), ctypes.byref(opts), _ptr(iters), _ptr(relres),
                                                 _ptr(status), _stream(stream)), "sspcg_solve_qp_batched_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# The QP step around the solve
+# ---------------------------------------------------------------------------
+def sspcg_form_gamma(N, nx, nu, A, B, qd, rd, c, q, r, gamma, stream=None):
+    _check(lib().sspcg_form_gamma(N, nx, nu, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(c), _ptr(q), _ptr(r),
+                                  _ptr(gamma), _stream(stream)), "sspcg_form_gamma")
+
+
+def sspcg_recover_step(N, nx, nu, A, B, qd, rd, q, r, mu, dx, du, stream=None):
+    _check(lib().sspcg_recover_step(N, nx, nu, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(q), _ptr(r), _ptr(mu),
+                                    _ptr(dx), _ptr(du), _stream(stream)), "sspcg_recover_step")
+
+
+def sspcg_form_gamma_batched(plan, A, B, qd, rd, c, q, r, gamma, stream=None):
+    _check(lib().sspcg_form_gamma_batched(plan.handle, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(c), _ptr(q),
+                                          _ptr(r), _ptr(gamma), _stream(stream)), "sspcg_form_gamma_batched")
+
+
+def sspcg_recover_step_batched(plan, A, B, qd, rd, q, r, mu, dx, du, stream=None):
+    _check(lib().sspcg_recover_step_batched(plan.handle, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(q), _ptr(r),
+                                            _ptr(mu), _ptr(dx), _ptr(du), _stream(stream)),
+           "sspcg_recover_step_batched")
 
 
 # ---------------------------------------------------------------------------
