@@ -323,6 +323,29 @@ sspcg_status sspcg_pipeline_host(sspcg_plan *plan, sspcg_precond kind, const flo
                                  float *lambda_host, int32_t *iters_host, double *relres_host, int32_t *status_host,
                                  sspcg_stream stream);
 
+/*
+ * sspcg_pipeline_host without the final wait: call i copies its inputs into
+ * plan-owned device slot i % 2 on a plan copy stream, runs the path on
+ * ``stream``, and copies the results to the host buffers on a second plan
+ * copy stream, so that one call's copies overlap the previous call's
+ * compute.  Computes of successive calls run in call order even on
+ * different streams.  The host buffers should be pinned (pageable ones
+ * work but serialise the copies) and stay untouched until the results are
+ * complete: after sspcg_plan_join(plan, s) once stream s has completed.
+ * Inputs are only read, so calls may share them; with options.warm_start
+ * lambda_host is read as the starting point when the call's copies run,
+ * which is not ordered after an earlier in-flight call's copy-out, so a
+ * warm-started call that must start from the previous result joins first.
+ * Allocates on first use two slots of inputs and outputs and one set of
+ * D, E, PD, PE blocks, kept until sspcg_plan_destroy.
+ */
+sspcg_status sspcg_pipeline_host_async(sspcg_plan *plan, sspcg_precond kind, const float *A_host,
+                                       const float *B_host, const float *qd_host, const float *rd_host,
+                                       const float *gamma_host, float *lambda_host, int32_t *iters_host,
+                                       double *relres_host, int32_t *status_host, sspcg_stream stream);
+/* Make ``stream`` wait for every copy of the plan's earlier asynchronous host pipeline calls. */
+sspcg_status sspcg_plan_join(sspcg_plan *plan, sspcg_stream stream);
+
 /* ------------------------------------------------------------------ */
 /* Batched solve without allocation                                   */
 /* ------------------------------------------------------------------ */

@@ -224,6 +224,16 @@ struct sspcg_plan {
   int64_t hbuf_floats = 0;
   int32_t *hint = nullptr;
   double *hdbl = nullptr;
+  // asynchronous host pipeline: two input/output slots, shared block buffers, copy streams
+  struct AsyncSlot {
+    float *buf = nullptr;  // A, B, qd, rd, gamma, lambda
+    int32_t *ints = nullptr;
+    double *dbl = nullptr;
+    cudaEvent_t in_ready = nullptr, consumed = nullptr, computed = nullptr, out_done = nullptr;
+  } aslot[2];
+  float *ablocks = nullptr;  // D, E, PD, PE
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  int64_t acalls = 0;
 };
 
 namespace {
@@ -242,6 +252,16 @@ void plan_free(sspcg_plan *p) {
       cudaFree(g.d_refs);
       cudaFree(g.d_orefs);
     }
+  for (auto &a : p->aslot) {
+    cudaFree(a.buf);
+    cudaFree(a.ints);
+    cudaFree(a.dbl);
+    for (cudaEvent_t e : {a.in_ready, a.consumed, a.computed, a.out_done})
+      if (e) cudaEventDestroy(e);
+  }
+  cudaFree(p->ablocks);
+  if (p->h2d) cudaStreamDestroy(p->h2d);
+  if (p->d2h) cudaStreamDestroy(p->d2h);
   for (auto s : p->side) cudaStreamDestroy(s);
   for (auto e : p->ev) cudaEventDestroy(e);
   for (auto s : p->lanes) cudaStreamDestroy(s);
@@ -1066,6 +1086,94 @@ sspcg_status sspcg_pipeline_host(sspcg_plan *plan, sspcg_precond kind, const flo
   SSPCG_CUDA(cudaMemcpyAsync(status_host, status, sizeof(int32_t) * plan->nprob, cudaMemcpyDeviceToHost, st));
   SSPCG_CUDA(cudaMemcpyAsync(relres_host, relres, sizeof(double) * plan->nprob, cudaMemcpyDeviceToHost, st));
   SSPCG_CUDA(cudaStreamSynchronize(st));
+  return SSPCG_OK;
+}
+
+// Asynchronous host pipeline: call i copies its inputs into slot i % 2 on the plan's copy stream (after
+// the compute that last read that slot), computes on ``stream`` (after its copies and after the copy-out
+// that last read that slot's outputs), and copies its results out on the plan's second copy stream.  So
+// the copies of one call overlap the compute of the previous one.
+static sspcg_status async_setup(sspcg_plan *p) {
+  const int64_t *sz = p->sizes;
+  auto r4 = [](int64_t n) { return round_up(std::max<int64_t>(n, 4), 4); };
+  if (!p->ablocks) {
+    SSPCG_CUDA(cudaMalloc(&p->ablocks, sizeof(float) * (2 * r4(sz[SSPCG_ARRAY_DIAG]) + 2 * r4(sz[SSPCG_ARRAY_OFF]))));
+    SSPCG_CUDA(cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking));
+    SSPCG_CUDA(cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking));
+    const int64_t in = r4(sz[SSPCG_ARRAY_A]) + r4(sz[SSPCG_ARRAY_B]) + r4(sz[SSPCG_ARRAY_QD]) + r4(sz[SSPCG_ARRAY_RD]) +
+                       2 * r4(sz[SSPCG_ARRAY_VEC]);
+    for (auto &a : p->aslot) {
+      SSPCG_CUDA(cudaMalloc(&a.buf, sizeof(float) * in));
+      SSPCG_CUDA(cudaMalloc(&a.ints, sizeof(int32_t) * 2 * p->nprob));
+      SSPCG_CUDA(cudaMalloc(&a.dbl, sizeof(double) * p->nprob));
+      for (cudaEvent_t *e : {&a.in_ready, &a.consumed, &a.computed, &a.out_done})
+        SSPCG_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+  }
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_pipeline_host_async(sspcg_plan *plan, sspcg_precond kind, const float *A_host,
+                                       const float *B_host, const float *qd_host, const float *rd_host,
+                                       const float *gamma_host, float *lambda_host, int32_t *iters_host,
+                                       double *relres_host, int32_t *status_host, sspcg_stream stream) {
+  if (!plan || kind < 0 || kind > 3) return SSPCG_ERR_INVALID_ARG;
+  if (plan->nprob == 0) return SSPCG_OK;
+  if (!qd_host || !gamma_host || !lambda_host || !iters_host || !relres_host || !status_host)
+    return SSPCG_ERR_INVALID_ARG;
+  sspcg_status s = async_setup(plan);
+  if (s != SSPCG_OK) return s;
+  const int64_t *sz = plan->sizes;
+  auto r4 = [](int64_t n) { return round_up(std::max<int64_t>(n, 4), 4); };
+  sspcg_plan::AsyncSlot &a = plan->aslot[plan->acalls & 1];
+  float *cur = a.buf;
+  auto take = [&](int64_t n) { float *r = cur; cur += r4(n); return r; };
+  float *A = take(sz[SSPCG_ARRAY_A]), *B = take(sz[SSPCG_ARRAY_B]), *qd = take(sz[SSPCG_ARRAY_QD]);
+  float *rd = take(sz[SSPCG_ARRAY_RD]), *g = take(sz[SSPCG_ARRAY_VEC]), *lam = take(sz[SSPCG_ARRAY_VEC]);
+  float *D = plan->ablocks, *E = D + r4(sz[SSPCG_ARRAY_DIAG]), *PD = E + r4(sz[SSPCG_ARRAY_OFF]);
+  float *PE = PD + r4(sz[SSPCG_ARRAY_DIAG]);
+  int32_t *iters = a.ints, *status = a.ints + plan->nprob;
+  double *relres = a.dbl;
+  cudaStream_t st = (cudaStream_t)stream;
+  // inputs: after the compute that last read this slot
+  SSPCG_CUDA(cudaStreamWaitEvent(plan->h2d, a.consumed, 0));
+  auto h2d = [&](float *dst, const float *src, int64_t n) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyHostToDevice, plan->h2d);
+  };
+  cudaError_t e;
+  if ((e = h2d(A, A_host, sz[SSPCG_ARRAY_A])) != cudaSuccess) return cuda_fail(e);
+  if ((e = h2d(B, B_host, sz[SSPCG_ARRAY_B])) != cudaSuccess) return cuda_fail(e);
+  if ((e = h2d(qd, qd_host, sz[SSPCG_ARRAY_QD])) != cudaSuccess) return cuda_fail(e);
+  if ((e = h2d(rd, rd_host, sz[SSPCG_ARRAY_RD])) != cudaSuccess) return cuda_fail(e);
+  if ((e = h2d(g, gamma_host, sz[SSPCG_ARRAY_VEC])) != cudaSuccess) return cuda_fail(e);
+  if (plan->opts.warm_start && (e = h2d(lam, lambda_host, sz[SSPCG_ARRAY_VEC])) != cudaSuccess) return cuda_fail(e);
+  SSPCG_CUDA(cudaEventRecord(a.in_ready, plan->h2d));
+  // compute: after its inputs, after the copy-out that last read this slot's outputs, and after the
+  // previous call's compute (the D, E, PD, PE blocks are shared), whatever stream that one ran on
+  SSPCG_CUDA(cudaStreamWaitEvent(st, a.in_ready, 0));
+  SSPCG_CUDA(cudaStreamWaitEvent(st, a.out_done, 0));
+  SSPCG_CUDA(cudaStreamWaitEvent(st, plan->aslot[(plan->acalls + 1) & 1].computed, 0));
+  s = sspcg_pipeline_batched(plan, kind, A, B, qd, rd, g, D, E, PD, PE, lam, iters, relres, status, stream);
+  if (s != SSPCG_OK) return s;
+  SSPCG_CUDA(cudaEventRecord(a.consumed, st));
+  SSPCG_CUDA(cudaEventRecord(a.computed, st));
+  // outputs
+  SSPCG_CUDA(cudaStreamWaitEvent(plan->d2h, a.computed, 0));
+  SSPCG_CUDA(cudaMemcpyAsync(lambda_host, lam, sizeof(float) * sz[SSPCG_ARRAY_VEC], cudaMemcpyDeviceToHost,
+                             plan->d2h));
+  SSPCG_CUDA(cudaMemcpyAsync(iters_host, iters, sizeof(int32_t) * plan->nprob, cudaMemcpyDeviceToHost, plan->d2h));
+  SSPCG_CUDA(cudaMemcpyAsync(status_host, status, sizeof(int32_t) * plan->nprob, cudaMemcpyDeviceToHost, plan->d2h));
+  SSPCG_CUDA(cudaMemcpyAsync(relres_host, relres, sizeof(double) * plan->nprob, cudaMemcpyDeviceToHost, plan->d2h));
+  SSPCG_CUDA(cudaEventRecord(a.out_done, plan->d2h));
+  ++plan->acalls;
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_plan_join(sspcg_plan *plan, sspcg_stream stream) {
+  if (!plan) return SSPCG_ERR_INVALID_ARG;
+  if (!plan->d2h) return SSPCG_OK;
+  for (auto &a : plan->aslot) SSPCG_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, a.out_done, 0));
   return SSPCG_OK;
 }
 

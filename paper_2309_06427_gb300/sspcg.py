@@ -96,6 +96,8 @@ def lib() -> ctypes.CDLL:
             "sspcg_residual_qp_batched": [_VP] * 9,
             "sspcg_pipeline_batched": [_VP, _I32] + [_VP] * 14,
             "sspcg_pipeline_host": [_VP, _I32] + [_VP] * 10,
+            "sspcg_pipeline_host_async": [_VP, _I32] + [_VP] * 10,
+            "sspcg_plan_join": [_VP, _VP],
             "sspcg_solve_qp_batched_noalloc": [_I32] + [_VP] * 11 + [ctypes.POINTER(Options)] + [_VP] * 4,
             "sspcg_mlp_create": [ctypes.POINTER(_VP), _I32],
             "sspcg_mlp_destroy": [_VP],
@@ -340,6 +342,20 @@ def sspcg_pipeline_host(plan: Plan, kind, A, B, qd, rd, gamma, lam, iters, relre
     hp = lambda t: t.data_ptr() if t is not None else None
     _check(lib().sspcg_pipeline_host(plan.handle, k, hp(A), hp(B), hp(qd), hp(rd), hp(gamma), hp(lam), hp(iters),
                                      hp(relres), hp(status), _stream(stream)), "sspcg_pipeline_host")
+
+
+def sspcg_pipeline_host_async(plan: Plan, kind, A, B, qd, rd, gamma, lam, iters, relres, status, stream=None):
+    """Host-buffer pipeline without the final wait (pinned host tensors; complete after sspcg_plan_join and a
+    synchronisation of that stream)."""
+    k = PRECOND[kind] if isinstance(kind, str) else int(kind)
+    hp = lambda t: t.data_ptr() if t is not None else None
+    _check(lib().sspcg_pipeline_host_async(plan.handle, k, hp(A), hp(B), hp(qd), hp(rd), hp(gamma), hp(lam),
+                                           hp(iters), hp(relres), hp(status), _stream(stream)),
+           "sspcg_pipeline_host_async")
+
+
+def sspcg_plan_join(plan: Plan, stream=None):
+    _check(lib().sspcg_plan_join(plan.handle, _stream(stream)), "sspcg_plan_join")
 
 
 def sspcg_solve_qp_batched_noalloc(N, nx, nu, A, B, qd, rd, PD, PE, gamma, lam, opts: Options, iters, relres, status,

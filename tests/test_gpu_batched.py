@@ -94,6 +94,43 @@ def test_host_buffer_pipeline_matches_device_pipeline():
     assert torch.equal(lam, b.lam.cpu()) and torch.equal(it, b.iters.cpu())
 
 
+def _host_outputs(plan):
+    return (torch.zeros(max(int(plan.sizes[sspcg.ARRAY_VEC]), 4)).pin_memory(),
+            torch.zeros(plan.nprob, dtype=torch.int32).pin_memory(),
+            torch.zeros(plan.nprob, dtype=torch.float64).pin_memory(),
+            torch.zeros(plan.nprob, dtype=torch.int32).pin_memory())
+
+
+@pytest.mark.parametrize("streams", [1, 2])
+def test_async_host_pipeline_matches_synchronous(streams):
+    """Five overlapped calls with different gamma (two device slots reused), on one stream or alternating
+    between two: each call's results equal the synchronous host pipeline's bit for bit."""
+    probs = _ragged()[:40]
+    plan = _plan(probs)
+    b = sspcg.Batch(plan, probs, pin=True)
+    h = b.host
+    calls = 5
+    gammas = [torch.from_numpy(plan.pack(sspcg.ARRAY_VEC, [P.perturb_gamma(p, r) for p in probs])).pin_memory()
+              for r in range(calls)]
+    ref = []
+    for r in range(calls):
+        out = _host_outputs(plan)
+        sspcg.sspcg_pipeline_host(plan, "sym", h["A"], h["B"], h["qd"], h["rd"], gammas[r], *out)
+        ref.append(out)
+    ss = [torch.cuda.Stream() for _ in range(streams)]
+    got = [_host_outputs(plan) for _ in range(calls)]
+    for r in range(calls):
+        sspcg.sspcg_pipeline_host_async(plan, "sym", h["A"], h["B"], h["qd"], h["rd"], gammas[r], *got[r],
+                                        stream=ss[r % streams])
+    sspcg.sspcg_plan_join(plan, ss[0])
+    ss[0].synchronize()
+    for r in range(calls):
+        assert (got[r][3] == 0).all()
+        for x, y in zip(got[r], ref[r]):
+            assert torch.equal(x, y), r
+    assert not torch.equal(got[0][0], got[1][0])
+
+
 def test_full_size_ragged_batch_sampled_against_oracle():
     """All 4096 problems of the ragged workload, in the benchmark's launch configuration;
     48 sampled problems against the oracle one by one, and properties on every problem."""
