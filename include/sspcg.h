@@ -126,7 +126,21 @@ typedef struct {
   int32_t schedule;        /* SSPCG_SCHED_*; RESIDENT is downgraded to STREAM for problems that do not fit */
   int32_t block_threads;   /* threads per CTA, multiple of 32 in [32, 512]; 0: chosen by the library */
   int32_t precision;       /* SSPCG_PRECISION_*: working precision of the batched pipeline calls */
+  int32_t poly_degree;     /* d in [0, SSPCG_MAX_POLY_DEGREE]: the PCG applies the degree-d polynomial
+                              (Neumann) preconditioner of the splitting S = Phi - (Phi - S) with Phi^-1 the
+                              assembled preconditioner (Eq. polynomial_precon):
+                                Phi_d^-1 = sum_{j=0..d} (I - Phi^-1 S)^j Phi^-1.
+                              d = 0 is Phi^-1 itself.  Applied as z <- z + Phi^-1 (r - S z), d times after
+                              z = Phi^-1 r: d more products with S and with Phi^-1 per iteration, one more
+                              vector of shared memory.  Symmetric for every d; positive definite when the
+                              splitting converges (rho(I - Phi^-1 S) < 1, true for the symmetric stair, the
+                              additive stair and block-Jacobi; for scalar Jacobi only when 2 diag(S) - S is
+                              positive definite), and then eig(Phi_d^-1 S) = 1 - (1 - theta)^(d+1) for the
+                              eigenvalues theta of Phi^-1 S.  On the symmetric stair, degree d equals degree
+                              2d+1 on the block-Jacobi splitting. */
 } sspcg_options;
+
+#define SSPCG_MAX_POLY_DEGREE 16
 
 /* Message of the last CUDA error seen by this thread (static storage, never NULL). */
 const char *sspcg_last_cuda_error(void);

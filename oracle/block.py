@@ -52,8 +52,13 @@ def lib() -> ctypes.CDLL:
         L.oracle_build_schur.argtypes = [i, i, i, P, P, P, P, P, P, P]
         L.oracle_build_precond.argtypes = [i, i, i, P, P, P, P, P, P]
         L.oracle_pcg.argtypes = [i, i, P, P, P, P, P, P, P, P, i, d, i, PI, P, P]
+        L.oracle_pcg_poly.argtypes = [i, i, P, P, P, P, P, P, i, P, P, i, d, i, PI, P, P]
+        L.oracle_apply_poly.argtypes = [i, i, P, P, P, P, P, P, i, P, P]
         L.oracle_solve_batch.argtypes = [i, PI, PI, PI, PL, PL, PL, PL, PL, P, P, P, P, P, i, d, i, P, PI, P, PI, i]
-        for f in (L.oracle_build_schur, L.oracle_build_precond, L.oracle_pcg, L.oracle_solve_batch):
+        L.oracle_solve_batch_poly.argtypes = [i, PI, PI, PI, PL, PL, PL, PL, PL, P, P, P, P, P, i, i, d, i, P, PI, P,
+                                              PI, i]
+        for f in (L.oracle_build_schur, L.oracle_build_precond, L.oracle_pcg, L.oracle_pcg_poly,
+                  L.oracle_apply_poly, L.oracle_solve_batch, L.oracle_solve_batch_poly):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -116,27 +121,39 @@ def build_precond(S: BlockTridiag, kind: str | int = "sym") -> BlockTridiag:
     return BlockTridiag(d, l, u)
 
 
-def pcg(S: BlockTridiag, M: BlockTridiag, gamma, tol: float, max_iter: int | None = None, x0=None):
-    """Returns (x [N+1, nx], iters, relres, true_relres, status)."""
+def pcg(S: BlockTridiag, M: BlockTridiag, gamma, tol: float, max_iter: int | None = None, x0=None, degree: int = 0):
+    """Returns (x [N+1, nx], iters, relres, true_relres, status).  degree > 0: the degree-d polynomial
+    preconditioner of the splitting S = Psi - P with Psi^-1 = M (Eq. polynomial_precon)."""
     g = _f64(gamma).reshape(S.N + 1, S.nx)
     x = np.zeros_like(g) if x0 is None else _f64(x0).reshape(g.shape).copy()
     it = ctypes.c_int(0); rr = ctypes.c_double(0); tr = ctypes.c_double(0)
     mi = 10 * (S.N + 1) * S.nx if max_iter is None else int(max_iter)
-    st = lib().oracle_pcg(S.N, S.nx, _p(S.d), _p(S.l), _p(S.u), _p(M.d), _p(M.l), _p(M.u), _p(g), _p(x),
-                          0 if x0 is None else 1, float(tol), mi, ctypes.byref(it), ctypes.byref(rr),
-                          ctypes.byref(tr))
+    st = lib().oracle_pcg_poly(S.N, S.nx, _p(S.d), _p(S.l), _p(S.u), _p(M.d), _p(M.l), _p(M.u), int(degree), _p(g),
+                               _p(x), 0 if x0 is None else 1, float(tol), mi, ctypes.byref(it), ctypes.byref(rr),
+                               ctypes.byref(tr))
     return x, it.value, rr.value, tr.value, st
 
 
-def solve_problem(p, kind="sym", tol=1e-6, max_iter=None, x0=None):
+def apply_poly(S: BlockTridiag, M: BlockTridiag, degree: int, r) -> np.ndarray:
+    """z = sum_{j<=degree} (Psi^-1 P)^j Psi^-1 r with Psi^-1 = M, P = Psi - S (Eq. polynomial_precon)."""
+    r = _f64(r).reshape(S.N + 1, S.nx)
+    z = np.zeros_like(r)
+    rc = lib().oracle_apply_poly(S.N, S.nx, _p(S.d), _p(S.l), _p(S.u), _p(M.d), _p(M.l), _p(M.u), int(degree), _p(r),
+                                 _p(z))
+    if rc != OK:
+        raise ValueError(f"oracle_apply_poly failed: {rc}")
+    return z
+
+
+def solve_problem(p, kind="sym", tol=1e-6, max_iter=None, x0=None, degree=0):
     """Whole path for one ``problems.Problem``: returns (S, M, x, iters, relres, true_relres, status)."""
     S = build_schur(p.A, p.B, p.qd, p.rd)
     M = build_precond(S, kind)
-    x, it, rr, tr, st = pcg(S, M, p.gamma, tol, max_iter, x0)
+    x, it, rr, tr, st = pcg(S, M, p.gamma, tol, max_iter, x0, degree)
     return S, M, x, it, rr, tr, st
 
 
-def solve_batch(problems, kind="sym", tol=1e-6, max_iter=0, nthreads=0):
+def solve_batch(problems, kind="sym", tol=1e-6, max_iter=0, nthreads=0, degree=0):
     """Whole path for a list of problems (OpenMP over problems).
 
     Returns (list of x arrays, iters, relres, status, threads_used, seconds).
@@ -164,9 +181,9 @@ def solve_batch(problems, kind="sym", tol=1e-6, max_iter=0, nthreads=0):
     PL = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     k = KINDS[kind] if isinstance(kind, str) else int(kind)
     t0 = time.perf_counter()
-    used = lib().oracle_solve_batch(nprob, PI(Ns), PI(nxs), PI(nus), PL(oA), PL(oB), PL(oq), PL(orr), PL(og),
-                                    _p(A), _p(B), _p(q), _p(r), _p(g), k, float(tol), int(max_iter), _p(x),
-                                    PI(iters), _p(relres), PI(status), int(nthreads))
+    used = lib().oracle_solve_batch_poly(nprob, PI(Ns), PI(nxs), PI(nus), PL(oA), PL(oB), PL(oq), PL(orr), PL(og),
+                                         _p(A), _p(B), _p(q), _p(r), _p(g), k, int(degree), float(tol),
+                                         int(max_iter), _p(x), PI(iters), _p(relres), PI(status), int(nthreads))
     dt = time.perf_counter() - t0
     xs = [x[og[i]:og[i] + problems[i].gamma.size].reshape(problems[i].gamma.shape) for i in range(nprob)]
     return xs, iters, relres, status, used, dt

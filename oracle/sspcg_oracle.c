@@ -25,6 +25,13 @@
  *   Sec. II-B: PCG, written as the textbook algorithm the paper cites
  *   (Saad, Iterative Methods for Sparse Linear Systems, Alg. 9.1).
  *
+ *   Sec. II-C, Eq. (polynomial_precon): for a splitting S = Psi - P,
+ *   Phi^-1 = (I + Psi^-1 P + (Psi^-1 P)^2 + ...) Psi^-1, truncated after the
+ *   degree-d term.  Psi^-1 is one of the preconditioners above (so Psi is
+ *   the matrix whose inverse that preconditioner is) and P = Psi - S, so
+ *   Psi^-1 P t = t - Psi^-1 S t: each term follows from the previous one
+ *   with one product by S and one by Psi^-1.
+ *
  * Block-tridiagonal storage used here (row-major nx*nx blocks, FP64):
  *   d[k] = M(k, k)     k = 0..N
  *   l[k] = M(k, k-1)   k = 1..N   (slot 0 unused)
@@ -257,21 +264,56 @@ static double dot(size_t n, const double *a, const double *b) {
 }
 
 /*
- * Textbook PCG on S x = gamma with preconditioner M = Phi^-1 (both block-tridiagonal).
+ * z = sum_{j=0..degree} (Psi^-1 P)^j Psi^-1 r  (Eq. polynomial_precon), with
+ * Psi^-1 = M (pd, pl, pu) and P = Psi - S.  Term by term:
+ *   t_0 = Psi^-1 r,  t_j = Psi^-1 P t_{j-1} = t_{j-1} - Psi^-1 (S t_{j-1}),  z = sum_j t_j.
+ * t, s and ps are scratch vectors of the same length.  degree = 0: z = M r.
+ */
+static void apply_poly(int N, int m, const double *d, const double *l, const double *u, const double *pd,
+                       const double *pl, const double *pu, int degree, const double *r, double *z, double *t,
+                       double *s, double *ps) {
+    const size_t n = (size_t)(N + 1) * m;
+    bt_matvec(N, m, pd, pl, pu, r, t);
+    memcpy(z, t, sizeof(double) * n);
+    for (int j = 1; j <= degree; ++j) {
+        bt_matvec(N, m, d, l, u, t, s);     /* S t_{j-1} */
+        bt_matvec(N, m, pd, pl, pu, s, ps); /* Psi^-1 S t_{j-1} */
+        for (size_t i = 0; i < n; ++i) t[i] -= ps[i];
+        for (size_t i = 0; i < n; ++i) z[i] += t[i];
+    }
+}
+
+/* Exported for the tests: z = Phi_d^-1 r of the degree-d polynomial preconditioner. */
+int oracle_apply_poly(int N, int nx, const double *d, const double *l, const double *u, const double *pd,
+                      const double *pl, const double *pu, int degree, const double *r, double *z) {
+    if (N < 0 || nx < 1 || degree < 0) return OR_BADARG;
+    const size_t n = (size_t)(N + 1) * nx;
+    double *t = (double *)malloc(sizeof(double) * n), *s = (double *)malloc(sizeof(double) * n);
+    double *ps = (double *)malloc(sizeof(double) * n);
+    apply_poly(N, nx, d, l, u, pd, pl, pu, degree, r, z, t, s, ps);
+    free(t); free(s); free(ps);
+    return OR_OK;
+}
+
+/*
+ * Textbook PCG on S x = gamma with preconditioner M = Phi^-1 (both block-tridiagonal),
+ * or with its degree-d polynomial (apply_poly) when degree > 0.
  * x: in = x0 (used when warm != 0, else x0 = 0), out = solution.
  * Stops before an iteration when ||r||_2 <= tol * ||gamma||_2, or after max_iter
  * iterations.  iters = number of S*p products.  relres = ||r||_2 / ||gamma||_2 of the
  * recurrence residual; true_relres = ||gamma - S x||_2 / ||gamma||_2.
  * gamma = 0 returns x = 0 and zero iterations.
  */
-int oracle_pcg(int N, int nx, const double *d, const double *l, const double *u, const double *pd, const double *pl,
-               const double *pu, const double *gamma, double *x, int warm, double tol, int max_iter, int *iters,
-               double *relres, double *true_relres) {
-    if (N < 0 || nx < 1) return OR_BADARG;
+int oracle_pcg_poly(int N, int nx, const double *d, const double *l, const double *u, const double *pd,
+                    const double *pl, const double *pu, int degree, const double *gamma, double *x, int warm,
+                    double tol, int max_iter, int *iters, double *relres, double *true_relres) {
+    if (N < 0 || nx < 1 || degree < 0) return OR_BADARG;
     const int m = nx;
     const size_t n = (size_t)(N + 1) * m;
     double *r = (double *)malloc(sizeof(double) * n), *z = (double *)malloc(sizeof(double) * n);
     double *p = (double *)malloc(sizeof(double) * n), *w = (double *)malloc(sizeof(double) * n);
+    double *t = (double *)malloc(sizeof(double) * n), *s = (double *)malloc(sizeof(double) * n);
+    double *ps = (double *)malloc(sizeof(double) * n);
     int status = OR_OK, it = 0;
     const double gnorm = sqrt(dot(n, gamma, gamma));
     if (gnorm == 0.0) {
@@ -279,13 +321,13 @@ int oracle_pcg(int N, int nx, const double *d, const double *l, const double *u,
         *iters = 0;
         *relres = 0.0;
         if (true_relres) *true_relres = 0.0;
-        free(r); free(z); free(p); free(w);
+        free(r); free(z); free(p); free(w); free(t); free(s); free(ps);
         return OR_OK;
     }
     if (!warm) memset(x, 0, sizeof(double) * n);
     bt_matvec(N, m, d, l, u, x, w); /* r0 = gamma - S x0 */
     for (size_t i = 0; i < n; ++i) r[i] = gamma[i] - w[i];
-    bt_matvec(N, m, pd, pl, pu, r, z); /* z0 = M r0 */
+    apply_poly(N, m, d, l, u, pd, pl, pu, degree, r, z, t, s, ps); /* z0 = Phi^-1 r0 */
     memcpy(p, z, sizeof(double) * n);
     double rz = dot(n, r, z);
     double rnorm = sqrt(dot(n, r, r));
@@ -297,7 +339,7 @@ int oracle_pcg(int N, int nx, const double *d, const double *l, const double *u,
         const double alpha = rz / pw;
         for (size_t i = 0; i < n; ++i) x[i] += alpha * p[i];
         for (size_t i = 0; i < n; ++i) r[i] -= alpha * w[i];
-        bt_matvec(N, m, pd, pl, pu, r, z); /* z = M r */
+        apply_poly(N, m, d, l, u, pd, pl, pu, degree, r, z, t, s, ps); /* z = Phi^-1 r */
         const double rz_new = dot(n, r, z);
         const double beta = rz_new / rz;
         rz = rz_new;
@@ -313,8 +355,15 @@ int oracle_pcg(int N, int nx, const double *d, const double *l, const double *u,
         for (size_t i = 0; i < n; ++i) w[i] = gamma[i] - w[i];
         *true_relres = sqrt(dot(n, w, w)) / gnorm;
     }
-    free(r); free(z); free(p); free(w);
+    free(r); free(z); free(p); free(w); free(t); free(s); free(ps);
     return status;
+}
+
+int oracle_pcg(int N, int nx, const double *d, const double *l, const double *u, const double *pd, const double *pl,
+               const double *pu, const double *gamma, double *x, int warm, double tol, int max_iter, int *iters,
+               double *relres, double *true_relres) {
+    return oracle_pcg_poly(N, nx, d, l, u, pd, pl, pu, 0, gamma, x, warm, tol, max_iter, iters, relres,
+                           true_relres);
 }
 
 /*
@@ -323,11 +372,11 @@ int oracle_pcg(int N, int nx, const double *d, const double *l, const double *u,
  * x is packed like gamma.  OpenMP over problems when available.
  * Returns the number of threads used.
  */
-int oracle_solve_batch(int nprob, const int *N, const int *nx, const int *nu, const int64_t *offA,
-                       const int64_t *offB, const int64_t *offq, const int64_t *offr, const int64_t *offg,
-                       const double *A, const double *B, const double *qd, const double *rd, const double *gamma,
-                       int kind, double tol, int max_iter_or_0, double *x, int *iters, double *relres,
-                       int *status, int nthreads) {
+int oracle_solve_batch_poly(int nprob, const int *N, const int *nx, const int *nu, const int64_t *offA,
+                            const int64_t *offB, const int64_t *offq, const int64_t *offr, const int64_t *offg,
+                            const double *A, const double *B, const double *qd, const double *rd,
+                            const double *gamma, int kind, int degree, double tol, int max_iter_or_0, double *x,
+                            int *iters, double *relres, int *status, int nthreads) {
     int used = 1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -349,8 +398,8 @@ int oracle_solve_batch(int nprob, const int *N, const int *nx, const int *nu, co
         if (st == OR_OK) st = oracle_build_precond(N[p], m, kind, d, l, u, pd, pl, pu);
         if (st == OR_OK) {
             const int max_iter = max_iter_or_0 > 0 ? max_iter_or_0 : 10 * n1 * m;
-            st = oracle_pcg(N[p], m, d, l, u, pd, pl, pu, gamma + offg[p], x + offg[p], 0, tol, max_iter,
-                            &iters[p], &relres[p], NULL);
+            st = oracle_pcg_poly(N[p], m, d, l, u, pd, pl, pu, degree, gamma + offg[p], x + offg[p], 0, tol,
+                                 max_iter, &iters[p], &relres[p], NULL);
         } else {
             iters[p] = 0;
             relres[p] = NAN;
@@ -359,4 +408,13 @@ int oracle_solve_batch(int nprob, const int *N, const int *nx, const int *nu, co
         free(d); free(l); free(u); free(pd); free(pl); free(pu);
     }
     return used;
+}
+
+int oracle_solve_batch(int nprob, const int *N, const int *nx, const int *nu, const int64_t *offA,
+                       const int64_t *offB, const int64_t *offq, const int64_t *offr, const int64_t *offg,
+                       const double *A, const double *B, const double *qd, const double *rd, const double *gamma,
+                       int kind, double tol, int max_iter_or_0, double *x, int *iters, double *relres,
+                       int *status, int nthreads) {
+    return oracle_solve_batch_poly(nprob, N, nx, nu, offA, offB, offq, offr, offg, A, B, qd, rd, gamma, kind, 0,
+                                   tol, max_iter_or_0, x, iters, relres, status, nthreads);
 }

@@ -14,6 +14,8 @@
 //   alpha = (r.z) / (p.w)   block reduction
 //   x += alpha p, r -= alpha w, barrier
 //   z = Phi^-1 r, (r.z), (r.r) block reduction
+//     (degree-d polynomial preconditioner: z = Phi^-1 r, then d times
+//      e = S-residual r - S z, barrier, z += Phi^-1 e; the sums after the last)
 //   beta = (r.z)new / (r.z)old, p = z + beta p, barrier
 // Stop before an iteration once r.r <= tol^2 gamma.gamma.
 //
@@ -176,12 +178,13 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   const int p = d.id;  // output slot
   const int N = d.N, n = N + 1, nu = d.nu, R_ = n * NX, NUP = vec_stride(nu);
   const int tid = threadIdx.x, T = blockDim.x;
-  int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems);  // the host sized smem so that K >= 0
+  const int poly = a.poly;
+  int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems, poly > 0);  // the host sized smem so that K >= 0
   if (K > a.max_resident) K = a.max_resident;
   if (K < 0) K = 0;
   const int Ks = K < N ? K : N;
-  const PcgLayout L = pcg_layout(OP, K, N, NX, nu);
-  Real *sp = sm + L.p, *sr = sm + L.r, *sw = sm + L.w, *sx = sm + L.x, *sv = sm + L.v;
+  const PcgLayout L = pcg_layout(OP, K, N, NX, nu, poly > 0);
+  Real *sp = sm + L.p, *sr = sm + L.r, *sw = sm + L.w, *sx = sm + L.x, *sv = sm + L.v, *se = sm + L.e;
   Real *svu = sv + n * NXP;  // v_u block rows, stride NUP
   const float *gam = a.gamma + d.ovec;
   // lambda (global): read once for a warm start, written once at the end
@@ -315,6 +318,43 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
                  : bt_row<NX, false, Real>(V.gPD, V.gPE, NX, N, k, i, src);
   };
 
+  // sw = z = Phi_d^-1 sr (polynomial of degree d = poly), and the block sums (r.z, r.r) into rz_, rr_.
+  //   z = Phi^-1 r, then d times: e = r - S z, barrier, z += Phi^-1 e  (Eq. polynomial_precon:
+  //   sum_{j<=d} (I - Phi^-1 S)^j Phi^-1 r in Horner form).  Ends with a barrier (the block sum).
+  auto precondition = [&](Real &rz_, Real &rr_) {
+    AccT s2[2] = {R::zero(), R::zero()};
+    for (int row = tid; row < R_; row += T) {
+      int k, i;
+      const int si = vid(row, k, i);
+      const Real z = apply_P_row(sr, k, i);
+      const Real r = sr[si];
+      sw[si] = z;
+      if (poly == 0) s2[0] = R::fma(s2[0], r, z);
+      s2[1] = R::fma(s2[1], r, r);
+    }
+    for (int t = 0; t < poly; ++t) {
+      __syncthreads();  // z complete
+      apply_S_phase1(sw);
+      for (int row = tid; row < R_; row += T) {
+        int k, i;
+        const int si = vid(row, k, i);
+        se[si] = sr[si] - apply_S_row(sw, k, i);
+      }
+      __syncthreads();  // e complete
+      const bool last = t + 1 == poly;
+      for (int row = tid; row < R_; row += T) {
+        int k, i;
+        const int si = vid(row, k, i);
+        const Real z = sw[si] + apply_P_row(se, k, i);
+        sw[si] = z;
+        if (last) s2[0] = R::fma(s2[0], sr[si], z);
+      }
+    }
+    block_sum<R, 2>(s2, slots + 64);
+    rz_ = R::get(s2[0]);
+    rr_ = R::get(s2[1]);
+  };
+
   __syncthreads();  // staged blocks and reciprocals visible
 
   // ---- r0 = gamma - S x0, z0 = Phi^-1 r0, p0 = z0 ----
@@ -353,22 +393,9 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     }
   }
   __syncthreads();
-  AccT s2[2];
   Real rz, rr;
   for (int pass = 0; pass < 2; ++pass) {
-    s2[0] = R::zero(); s2[1] = R::zero();
-    for (int row = tid; row < R_; row += T) {
-      int k, i;
-      const int si = vid(row, k, i);
-      const Real z = apply_P_row(sr, k, i);
-      const Real r = sr[si];
-      sw[si] = z;
-      s2[0] = R::fma(s2[0], r, z);
-      s2[1] = R::fma(s2[1], r, r);
-    }
-    block_sum<R, 2>(s2, slots + 64);
-    rz = R::get(s2[0]);
-    rr = R::get(s2[1]);
+    precondition(rz, rr);
     // warm start with fallback: restart from zero if lambda_0 is no better than zero
     if (pass == 0 && warm && a.warm == 2 && !(rr < gg)) {
       for (int row = tid; row < R_; row += T) {
@@ -419,20 +446,9 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       sr[si] = rfma(-alpha, sw[si], sr[si]);
     }
     __syncthreads();
-    // z = Phi^-1 r, r.z, r.r
-    s2[0] = R::zero(); s2[1] = R::zero();
-    for (int row = tid; row < R_; row += T) {
-      int k, i;
-      const int si = vid(row, k, i);
-      const Real z = apply_P_row(sr, k, i);
-      const Real r = sr[si];
-      sw[si] = z;
-      s2[0] = R::fma(s2[0], r, z);
-      s2[1] = R::fma(s2[1], r, r);
-    }
-    block_sum<R, 2>(s2, slots + 64);
-    const Real rz_new = R::get(s2[0]);
-    rr = R::get(s2[1]);
+    // z = Phi_d^-1 r, r.z, r.r
+    Real rz_new;
+    precondition(rz_new, rr);
     const Real beta = rz_new / rz;
     rz = rz_new;
     for (int row = tid; row < R_; row += T) {

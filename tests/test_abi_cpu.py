@@ -54,6 +54,10 @@ def test_invalid_shapes_rejected_on_host(L):
     assert L.sspcg_solve(4, 4, vp, vp, vp, vp, vp, vp, ctypes.byref(bad), vp, vp, vp, None) == sspcg.ERR_INVALID_ARG
     bad = sspcg.options(tol=-1.0)
     assert L.sspcg_solve(4, 4, vp, vp, vp, vp, vp, vp, ctypes.byref(bad), vp, vp, vp, None) == sspcg.ERR_INVALID_ARG
+    for deg in (-1, sspcg.MAX_POLY_DEGREE + 1):
+        bad = sspcg.options(poly_degree=deg)
+        assert L.sspcg_solve(4, 4, vp, vp, vp, vp, vp, vp, ctypes.byref(bad), vp, vp, vp, None) == \
+            sspcg.ERR_INVALID_ARG
     # plan with a bad shape
     import numpy as np
     h = ctypes.c_void_p()
