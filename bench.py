@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--problems", type=int, default=0,
                     help="first N problems of the workload only (small profiler captures); 0: all")
     ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
+    ap.add_argument("--no-poly", action="store_true", help="skip the polynomial-preconditioner comparison")
     ap.add_argument("--train-problems", type=int, default=4096, help="training problems of the warm-start network")
     ap.add_argument("--train-epochs", type=int, default=6)
     ap.add_argument("--mpc", action="store_true",
@@ -323,6 +324,40 @@ def warm_start_comparison(args, torch, sspcg, stream, rank):
             "gpu_launches": args.steps * (2 * launches_plain + 5 * chunks)}
 
 
+def poly_comparison(args, torch, sspcg, stream, probs, w):
+    """Polynomial preconditioners (Eq. polynomial_precon) on the benchmark workload: the whole pipeline step
+    with Phi_d^-1 = sum_{j<=d} (I - Phi^-1 S)^j Phi^-1 for the symmetric stair at d = 0..3, and block-Jacobi
+    at d = 1 (the same preconditioner as the symmetric stair at d = 0, applied implicitly from D^-1 and S)."""
+    out = {}
+    for kind, deg in (("sym", 0), ("sym", 1), ("sym", 2), ("sym", 3), ("bj", 1)):
+        plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
+                                       sspcg.options(tol=w.tol, poly_degree=deg))
+        b = sspcg.Batch(plan, probs)
+        d = b.dev
+
+        def step():
+            sspcg.sspcg_pipeline_batched(plan, kind, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD,
+                                         b.PE, b.lam, b.iters, b.relres, b.status, stream)
+
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        it = b.iters.cpu().numpy()
+        out[f"{kind}_d{deg}"] = {"solves_per_s": len(probs) / (ms / 1e3), "ms_per_step": ms,
+                                 "iters_mean": float(it.mean()),
+                                 "all_converged": bool((b.status.cpu().numpy() == 0).all())}
+        del b, plan
+    return out
+
+
 def mpc_comparison(args, torch, sspcg, stream, rank):
     """MPC batch: 16384 problems (N ~ U{64..512}, nx ~ U{4..28}) whose gamma is perturbed by 1 % for each of
     ``--mpc-resolves`` sequential re-solves.  Blocks and preconditioner are built once (A, B, Q, R do not
@@ -548,6 +583,8 @@ def main():
                          "fp64_problems": stats["pipeline_f64"],
                          "pcg_launches_per_step": stats["pipeline_launches"]}
     line["build_ms_per_step"] = build_ms
+    if not args.no_poly:
+        line["polynomial_preconditioners"] = poly_comparison(args, torch, sspcg, stream, probs, w)
     if not args.no_warm_start:
         line["warm_start"] = warm_start_comparison(args, torch, sspcg, stream, rank)
     if args.mpc:
