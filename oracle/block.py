@@ -50,6 +50,7 @@ def lib() -> ctypes.CDLL:
         PL = ctypes.POINTER(ctypes.c_int64)
         i, d = ctypes.c_int, ctypes.c_double
         L.oracle_build_schur.argtypes = [i, i, i, P, P, P, P, P, P, P]
+        L.oracle_build_schur_full.argtypes = [i, i, i, P, P, P, P, P, P, P]
         L.oracle_build_precond.argtypes = [i, i, i, P, P, P, P, P, P]
         L.oracle_pcg.argtypes = [i, i, P, P, P, P, P, P, P, P, i, d, i, PI, P, P]
         L.oracle_pcg_poly.argtypes = [i, i, P, P, P, P, P, P, i, P, P, i, d, i, PI, P, P]
@@ -57,7 +58,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_solve_batch.argtypes = [i, PI, PI, PI, PL, PL, PL, PL, PL, P, P, P, P, P, i, d, i, P, PI, P, PI, i]
         L.oracle_solve_batch_poly.argtypes = [i, PI, PI, PI, PL, PL, PL, PL, PL, P, P, P, P, P, i, i, d, i, P, PI, P,
                                               PI, i]
-        for f in (L.oracle_build_schur, L.oracle_build_precond, L.oracle_pcg, L.oracle_pcg_poly,
+        for f in (L.oracle_build_schur, L.oracle_build_schur_full, L.oracle_build_precond, L.oracle_pcg, L.oracle_pcg_poly,
                   L.oracle_apply_poly, L.oracle_solve_batch, L.oracle_solve_batch_poly):
             f.restype = ctypes.c_int
         _lib = L
@@ -107,6 +108,23 @@ def build_schur(A, B, qd, rd) -> BlockTridiag:
     rc = lib().oracle_build_schur(N, nx, nu, _p(A), _p(B), _p(qd), _p(rd), _p(d), _p(l), _p(u))
     if rc != OK:
         raise ValueError(f"oracle_build_schur failed: {rc}")
+    return BlockTridiag(d, l, u)
+
+
+def build_schur_full(A, B, Q, R) -> BlockTridiag:
+    """S with full SPD cost blocks Q [N+1][nx][nx], R [N][nu][nu] (Sec. II-A formulas with matrix inverses)."""
+    A, B, Q = _f64(A), _f64(B), _f64(Q)
+    N, nx = Q.shape[0] - 1, Q.shape[1]
+    nu = B.shape[2] if N > 0 and B.ndim == 3 else 0
+    R = _f64(R).reshape(N, nu, nu) if N > 0 and nu > 0 else np.zeros(1)
+    A = A if A.size else np.zeros(1)
+    B = B if B.size else np.zeros(1)
+    d = np.zeros((N + 1, nx, nx)); l = np.zeros_like(d); u = np.zeros_like(d)
+    rc = lib().oracle_build_schur_full(N, nx, nu, _p(A), _p(B), _p(Q), _p(R), _p(d), _p(l), _p(u))
+    if rc == NOT_SPD:
+        raise np.linalg.LinAlgError("cost block not positive definite")
+    if rc != OK:
+        raise ValueError(f"oracle_build_schur_full failed: {rc}")
     return BlockTridiag(d, l, u)
 
 

@@ -8,7 +8,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   for the initial state (-x_0 + x_s = 0) and one per knot
   (A_k x_k + B_k u_k - x_{k+1} = 0).
 * ``schur``: S = C G^-1 C^T, the positive definite form of Eq. (schur)
-  (the footnote of Sec. II-A negates the paper's -C G^-1 C^T).
+  (the footnote of Sec. II-A negates the paper's -C G^-1 C^T).  ``kkt_full``,
+  ``schur_full``: the same with full SPD cost blocks Q_k, R_k.
 * ``stair_splittings``: Psi_l, P_l, Psi_r, P_r by the block patterns of
   Eq. (stair) (Psi_l keeps the off-diagonal blocks of the even 1-based block
   rows, Psi_r of the odd rows; S = Psi - P).
@@ -29,18 +30,27 @@ import scipy.linalg
 
 def kkt(A, B, qd, rd):
     """Dense (G, C) of the trajectory QP for diagonal Q_k = diag(qd[k]), R_k = diag(rd[k])."""
-    A, B, qd, rd = (np.asarray(a, dtype=np.float64) for a in (A, B, qd, rd))
-    N, nx = qd.shape[0] - 1, qd.shape[1]
+    qd, rd = np.asarray(qd, dtype=np.float64), np.asarray(rd, dtype=np.float64)
+    Q = np.stack([np.diag(q) for q in qd])
+    R = np.stack([np.diag(r) for r in rd]) if len(rd) else np.zeros((0, 0, 0))
+    return kkt_full(A, B, Q, R)
+
+
+def kkt_full(A, B, Q, R):
+    """Dense (G, C) of the trajectory QP with full SPD cost blocks Q [N+1][nx][nx], R [N][nu][nu]:
+    G = blockdiag(Q_0, R_0, ..., R_{N-1}, Q_N)."""
+    A, B, Q = (np.asarray(a, dtype=np.float64) for a in (A, B, Q))
+    N, nx = Q.shape[0] - 1, Q.shape[1]
     nu = B.shape[2] if N > 0 else 0
+    R = np.asarray(R, dtype=np.float64).reshape(N, nu, nu)
     nz = (N + 1) * nx + N * nu
     xo = lambda k: k * (nx + nu)           # column offset of x_k
     uo = lambda k: k * (nx + nu) + nx      # column offset of u_k
-    g = np.zeros(nz)
+    G = np.zeros((nz, nz))
     for k in range(N + 1):
-        g[xo(k):xo(k) + nx] = qd[k]
+        G[xo(k):xo(k) + nx, xo(k):xo(k) + nx] = Q[k]
         if k < N:
-            g[uo(k):uo(k) + nu] = rd[k]
-    G = np.diag(g)
+            G[uo(k):uo(k) + nu, uo(k):uo(k) + nu] = R[k]
     C = np.zeros(((N + 1) * nx, nz))
     C[0:nx, xo(0):xo(0) + nx] = -np.eye(nx)
     for k in range(N):
@@ -53,6 +63,12 @@ def kkt(A, B, qd, rd):
 
 def schur(A, B, qd, rd) -> np.ndarray:
     G, C = kkt(A, B, qd, rd)
+    return C @ np.linalg.solve(G, C.T)
+
+
+def schur_full(A, B, Q, R) -> np.ndarray:
+    """S = C G^-1 C^T with full SPD cost blocks."""
+    G, C = kkt_full(A, B, Q, R)
     return C @ np.linalg.solve(G, C.T)
 
 

@@ -22,6 +22,9 @@
  *   Sec. IV: Phi_sym^-1 = Psi_l^-1 + Psi_r^-1 - D^-1.
  *   Sec. II-C, Eq. (jacobi): Phi = diag(S) or Phi = block-diag(S).
  *
+ *   Sec. II-A with full SPD Q_k, R_k: the same formulas with matrix inverses
+ *   (oracle_build_schur_full).
+ *
  *   Sec. II-B: PCG, written as the textbook algorithm the paper cites
  *   (Saad, Iterative Methods for Sparse Linear Systems, Alg. 9.1).
  *
@@ -153,6 +156,68 @@ static int spd_inverse(int m, const double *M, double *inv) {
     }
     free(L);
     free(y);
+    return rc;
+}
+
+/*
+ * Sec. II-A block formulas with full SPD cost blocks (the paper writes Q_k^-1
+ * and R_k^-1 as matrices), then the SPD negation of the footnote.
+ * Q: [N+1][nx][nx]  R: [N][nu][nu]; inverses by Cholesky (spd_inverse).
+ *   phi_k   = A_k Q_k^-1
+ *   theta_k = -A_k Q_k^-1 A_k^T - B_k R_k^-1 B_k^T - Q_{k+1}^-1
+ * Returns OR_NOT_SPD when a Q_k or R_k is not positive definite.
+ */
+int oracle_build_schur_full(int N, int nx, int nu, const double *A, const double *B, const double *Q,
+                            const double *R, double *d, double *l, double *u) {
+    if (N < 0 || nx < 1 || nu < 0) return OR_BADARG;
+    const int m = nx;
+    const size_t blk = (size_t)m * m;
+    memset(d, 0, sizeof(double) * blk * (N + 1));
+    memset(l, 0, sizeof(double) * blk * (N + 1));
+    memset(u, 0, sizeof(double) * blk * (N + 1));
+    double *Qi = (double *)malloc(sizeof(double) * blk * (N + 1));
+    double *Ri = (double *)malloc(sizeof(double) * (size_t)(nu > 0 ? nu * nu : 1) * (N > 0 ? N : 1));
+    double *theta = (double *)malloc(sizeof(double) * blk), *phi = (double *)malloc(sizeof(double) * blk);
+    int rc = OR_OK;
+    for (int k = 0; k <= N && rc == OR_OK; ++k)
+        if (spd_inverse(m, Q + (size_t)k * blk, Qi + (size_t)k * blk) != 0) rc = OR_NOT_SPD;
+    for (int k = 0; k < N && nu > 0 && rc == OR_OK; ++k)
+        if (spd_inverse(nu, R + (size_t)k * nu * nu, Ri + (size_t)k * nu * nu) != 0) rc = OR_NOT_SPD;
+    if (rc == OR_OK) {
+        /* first diagonal block of S_paper is -Q_0^-1; negated: Q_0^-1 */
+        memcpy(d, Qi, sizeof(double) * blk);
+        for (int k = 0; k < N; ++k) {
+            const double *Ak = A + (size_t)k * m * m, *Bk = B + (size_t)k * m * nu;
+            const double *Qk = Qi + (size_t)k * blk, *Qk1 = Qi + (size_t)(k + 1) * blk;
+            const double *Rk = Ri + (size_t)k * nu * nu;
+            /* phi_k = A_k Q_k^-1 */
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < m; ++j) {
+                    double s = 0.0;
+                    for (int t = 0; t < m; ++t) s += Ak[i * m + t] * Qk[t * m + j];
+                    phi[i * m + j] = s;
+                }
+            /* theta_k = -phi_k A_k^T - (B_k R_k^-1) B_k^T - Q_{k+1}^-1 */
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < m; ++j) {
+                    double s = 0.0;
+                    for (int t = 0; t < m; ++t) s += phi[i * m + t] * Ak[j * m + t];
+                    double sb = 0.0;
+                    for (int a = 0; a < nu; ++a) {
+                        double br = 0.0;
+                        for (int b = 0; b < nu; ++b) br += Bk[i * nu + b] * Rk[b * nu + a];
+                        sb += br * Bk[j * nu + a];
+                    }
+                    theta[i * m + j] = -s - sb - Qk1[i * m + j];
+                }
+            for (size_t e = 0; e < blk; ++e) {
+                BLK(d, k + 1, m)[e] = -theta[e];
+                BLK(l, k + 1, m)[e] = -phi[e];
+            }
+            transpose(m, BLK(l, k + 1, m), BLK(u, k, m));
+        }
+    }
+    free(Qi); free(Ri); free(theta); free(phi);
     return rc;
 }
 

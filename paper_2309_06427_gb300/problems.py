@@ -252,3 +252,19 @@ def qp_vectors(p: Problem, seed: int = 0):
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     return (f32(z[:n * m].reshape(n, m)), f32(z[n * m:2 * n * m].reshape(n, m)),
             f32(z[2 * n * m:].reshape(p.N, u)))
+
+
+def full_cost(p: Problem, seed: int = 0):
+    """Full SPD cost blocks of problem ``p`` (FP32, exactly symmetric):
+    Q_k = diag(qd_k) + M_k M_k^T / nx  [N+1, nx, nx],  R_k = diag(rd_k) + W_k W_k^T / nu  [N, nu, nu],
+    M_k, W_k with N(0, 1) entries from stream ``p.key + (seed + 1) * 2**52`` (all M_k, then all W_k).
+    The diagonal of p is kept, so Q_k >= diag(qd_k) and the coupling is of the same size."""
+    n, m, u = p.N + 1, p.nx, p.nu
+    z = normals(p.key + ((seed + 1) << 52), n * m * m + p.N * u * u, 0)
+    M = z[:n * m * m].reshape(n, m, m)
+    W = z[n * m * m:].reshape(p.N, u, u)
+    Q = np.einsum("kij,klj->kil", M, M) / m + np.einsum("ki,ij->kij", p.qd.astype(np.float64), np.eye(m))
+    R = (np.einsum("kij,klj->kil", W, W) / max(u, 1) +
+         np.einsum("ki,ij->kij", p.rd.astype(np.float64), np.eye(u))) if p.N > 0 else np.zeros((0, u, u))
+    sym = lambda a: np.ascontiguousarray((a + np.swapaxes(a, 1, 2)) * 0.5, dtype=np.float32)
+    return sym(Q), sym(R)
