@@ -78,6 +78,7 @@ def parse():
                     help="first N problems of the workload only (small profiler captures); 0: all")
     ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--no-poly", action="store_true", help="skip the polynomial-preconditioner comparison")
+    ap.add_argument("--no-full", action="store_true", help="skip the full-cost-block comparison")
     ap.add_argument("--train-problems", type=int, default=4096, help="training problems of the warm-start network")
     ap.add_argument("--train-epochs", type=int, default=6)
     ap.add_argument("--mpc", action="store_true",
@@ -358,6 +359,51 @@ def poly_comparison(args, torch, sspcg, stream, probs, w):
     return out
 
 
+def full_cost_comparison(args, torch, sspcg, stream, probs, w):
+    """Full SPD cost blocks (Q_k = diag(qd_k) + M M^T / nx, R_k likewise) on the benchmark workload: the whole
+    step (full-cost Schur build, symmetric stair, block-form PCG) against the same block-form step on the
+    diagonal-cost blocks."""
+    QR = [P.full_cost(p) for p in probs]
+    plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
+                                   sspcg.options(tol=w.tol))
+    b = sspcg.Batch(plan, probs)
+    d = b.dev
+    Q = torch.from_numpy(plan.pack(sspcg.ARRAY_DIAG, [q for q, _ in QR])).cuda()
+    R = torch.from_numpy(plan.pack(sspcg.ARRAY_RFULL, [r for _, r in QR])).cuda()
+    st_b = torch.zeros(plan.nprob, dtype=torch.int32, device="cuda")
+
+    def solve():
+        sspcg.sspcg_build_precond_batched(plan, PRECOND, b.D, b.E, b.PD, b.PE, st_b, stream)
+        sspcg.sspcg_solve_batched(plan, b.D, b.E, b.PD, b.PE, d["gamma"], b.lam, b.iters, b.relres, b.status, stream)
+
+    def full_step():
+        sspcg.sspcg_build_schur_full_batched(plan, d["A"], d["B"], Q, R, b.D, b.E, st_b, stream)
+        solve()
+
+    def diag_step():
+        sspcg.sspcg_build_schur_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.D, b.E, stream)
+        solve()
+
+    out = {}
+    for name, fn in (("full_cost", full_step), ("diagonal_cost", diag_step)):
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        it = b.iters.cpu().numpy()
+        out[name] = {"solves_per_s": len(probs) / (ms / 1e3), "ms_per_step": ms, "iters_mean": float(it.mean()),
+                     "all_converged": bool((b.status.cpu().numpy() == 0).all() and (st_b.cpu().numpy() == 0).all())}
+    out["operator"] = "block form (D, E); the factored QP form needs diagonal Q and R"
+    return out
+
+
 def mpc_comparison(args, torch, sspcg, stream, rank):
     """MPC batch: 16384 problems (N ~ U{64..512}, nx ~ U{4..28}) whose gamma is perturbed by 1 % for each of
     ``--mpc-resolves`` sequential re-solves.  Blocks and preconditioner are built once (A, B, Q, R do not
@@ -585,6 +631,8 @@ def main():
     line["build_ms_per_step"] = build_ms
     if not args.no_poly:
         line["polynomial_preconditioners"] = poly_comparison(args, torch, sspcg, stream, probs, w)
+    if not args.no_full:
+        line["full_cost_blocks"] = full_cost_comparison(args, torch, sspcg, stream, probs, w)
     if not args.no_warm_start:
         line["warm_start"] = warm_start_comparison(args, torch, sspcg, stream, rank)
     if args.mpc:

@@ -244,7 +244,8 @@ typedef enum {
   SSPCG_ARRAY_DIAG = 4, /* (N+1)*nx*nx: D and PD */
   SSPCG_ARRAY_OFF = 5,  /* N*nx*nx: E and PE */
   SSPCG_ARRAY_VEC = 6,  /* (N+1)*nx: gamma and lambda */
-  SSPCG_NUM_ARRAYS = 7
+  SSPCG_ARRAY_RFULL = 7, /* N*nu*nu: full R_k blocks (sspcg_build_schur_full_batched) */
+  SSPCG_NUM_ARRAYS = 8
 } sspcg_array;
 
 sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *N, const int32_t *nx,
@@ -279,6 +280,33 @@ sspcg_status sspcg_plan_timings(sspcg_plan *plan, float *out_ms);
 /* Batched sspcg_build_schur over packed arrays. */
 sspcg_status sspcg_build_schur_batched(sspcg_plan *plan, const float *A, const float *B, const float *qd,
                                        const float *rd, float *D, float *E, sspcg_stream stream);
+
+/*
+ * Schur blocks with full SPD cost blocks (Sec. II-A, where the block formulas
+ * carry Q_k^-1 and R_k^-1 as matrices):
+ *   D_0 = Q_0^-1,  D_{k+1} = A_k Q_k^-1 A_k^T + B_k R_k^-1 B_k^T + Q_{k+1}^-1,
+ *   E_k = S(k+1, k) = -A_k Q_k^-1.
+ * Q: FP32 [N+1][nx][nx], R: FP32 [N][nu][nu], row-major and symmetric (only
+ * the lower triangles are read).  Q_k^-1 and R_k^-1 are formed by FP64 LDL^T
+ * (as the D_k^-1 of sspcg_build_precond) and rounded to FP32 once; the products
+ * are FP32, D_k exactly symmetric.  The result feeds sspcg_build_precond and
+ * the block-form solves (sspcg_solve, sspcg_solve_batched); the QP-form calls
+ * take diagonal Q and R only.
+ * status (device int32, one per problem): 0, or SSPCG_SOLVE_NOT_SPD when a Q_k or
+ * R_k is not positive definite (that inverse is set to zero, so D and E are
+ * then meaningless).  The preconditioner build resets status: read it first.
+ * Single problem: work is caller-owned device scratch of
+ * sspcg_schur_full_work_floats(N, nx, nu) floats, 16-byte aligned.
+ * Batched: Q packed like D (SSPCG_ARRAY_DIAG), R in SSPCG_ARRAY_RFULL; the
+ * plan allocates its scratch on first use.
+ */
+sspcg_status sspcg_schur_full_work_floats(int32_t N, int32_t nx, int32_t nu, int64_t *floats);
+sspcg_status sspcg_build_schur_full(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *Q,
+                                    const float *R, float *D, float *E, float *work, int32_t *status,
+                                    sspcg_stream stream);
+sspcg_status sspcg_build_schur_full_batched(sspcg_plan *plan, const float *A, const float *B, const float *Q,
+                                            const float *R, float *D, float *E, int32_t *status,
+                                            sspcg_stream stream);
 
 /* Batched sspcg_build_precond; status: device int32[nprob]. */
 sspcg_status sspcg_build_precond_batched(sspcg_plan *plan, sspcg_precond kind, const float *D, const float *E,

@@ -237,6 +237,11 @@ struct sspcg_plan {
   float *ablocks = nullptr;  // D, E, PD, PE
   cudaStream_t h2d = nullptr, d2h = nullptr;
   int64_t acalls = 0;
+  // full SPD cost blocks: Q^-1 (laid out like D), R^-1 (like the R input), R-block groups by nu
+  float *qinv = nullptr, *rinv = nullptr;
+  int64_t *d_roff = nullptr;
+  std::vector<NxGroup> nxg_r;
+  bool full_ready = false;
 };
 
 namespace {
@@ -263,6 +268,14 @@ void plan_free(sspcg_plan *p) {
       if (e) cudaEventDestroy(e);
   }
   cudaFree(p->ablocks);
+  cudaFree(p->qinv);
+  cudaFree(p->rinv);
+  cudaFree(p->d_roff);
+  for (NxGroup &g : p->nxg_r) {
+    cudaFree(g.d_desc);
+    cudaFree(g.d_refs);
+    cudaFree(g.d_orefs);
+  }
   if (p->h2d) cudaStreamDestroy(p->h2d);
   if (p->d2h) cudaStreamDestroy(p->d2h);
   for (auto s : p->side) cudaStreamDestroy(s);
@@ -586,7 +599,8 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
   std::vector<int32_t> all, main_set, tiny;
   for (int32_t i = 0; i < nprob; ++i) {
     const int64_t n = N[i] + 1, m = nx[i], u = nu[i], Ni = N[i];
-    const int64_t sz[SSPCG_NUM_ARRAYS] = {Ni * m * m, Ni * m * u, n * m, Ni * u, n * m * m, Ni * m * m, n * m};
+    const int64_t sz[SSPCG_NUM_ARRAYS] = {Ni * m * m, Ni * m * u, n * m, Ni * u, n * m * m, Ni * m * m, n * m,
+                                          Ni * u * u};
     for (int k = 0; k < SSPCG_NUM_ARRAYS; ++k) {
       p->offsets[k][i] = cur[k];
       cur[k] += round_up(sz[k], 4);  // 16-byte aligned problem starts
@@ -760,6 +774,81 @@ sspcg_status sspcg_build_schur_batched(sspcg_plan *plan, const float *A, const f
   if (plan->total_off > 0 && (!A || !rd || !E || !B)) return SSPCG_ERR_INVALID_ARG;
   SSPCG_CUDA(launch_schur_build<float>(plan_set(plan), plan->d_kref, plan->total_knots, A, B, qd, rd, D, E,
                                        (cudaStream_t)stream, device_sms(), plan->mx));
+  return SSPCG_OK;
+}
+
+static int64_t schur_full_work(int32_t N, int32_t nx, int32_t nu) {
+  return round_up((int64_t)(N + 1) * nx * nx, 4) + (int64_t)N * nu * nu;
+}
+
+sspcg_status sspcg_schur_full_work_floats(int32_t N, int32_t nx, int32_t nu, int64_t *floats) {
+  if (!floats || !shape_ok(N, nx, nu)) return SSPCG_ERR_INVALID_ARG;
+  *floats = schur_full_work(N, nx, nu);
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_build_schur_full(int32_t N, int32_t nx, int32_t nu, const float *A, const float *B, const float *Q,
+                                    const float *R, float *D, float *E, float *work, int32_t *status,
+                                    sspcg_stream stream) {
+  if (!shape_ok(N, nx, nu)) return SSPCG_ERR_INVALID_ARG;
+  if (!Q || !D || !work || !status || (N > 0 && (!A || !E || (nu > 0 && (!B || !R))))) return SSPCG_ERR_INVALID_ARG;
+  if (!aligned16(work)) return SSPCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  float *qi = work, *ri = work + round_up((int64_t)(N + 1) * nx * nx, 4);
+  SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+  // Q_k^-1 and R_k^-1 by the FP64 LDL^T inversion of the preconditioner build (Q is laid out like D; the R
+  // blocks are N blocks of nu x nu, that is, the diagonal blocks of a problem with nx = nu and N - 1)
+  SSPCG_CUDA(launch_precond_inv<float>(ProbSet{nullptr, single_desc(N, nx, nu), 1}, nullptr, N + 1, nx,
+                                       (int)SSPCG_PRECOND_SYM_STAIR, Q, qi, status, st));
+  if (N > 0 && nu > 0)
+    SSPCG_CUDA(launch_precond_inv<float>(ProbSet{nullptr, single_desc(N - 1, nu, 0), 1}, nullptr, N, nu,
+                                         (int)SSPCG_PRECOND_SYM_STAIR, R, ri, status, st));
+  SSPCG_CUDA(launch_schur_full(ProbSet{nullptr, single_desc(N, nx, nu), 1}, nullptr, N + 1, nullptr, A, B, qi, ri, D,
+                               E, st, std::max(nx, nu)));
+  return SSPCG_OK;
+}
+
+static sspcg_status full_setup(sspcg_plan *p) {
+  if (p->full_ready) return SSPCG_OK;
+  SSPCG_CUDA(cudaMalloc(&p->qinv, sizeof(float) * std::max<int64_t>(p->sizes[SSPCG_ARRAY_DIAG], 4)));
+  SSPCG_CUDA(cudaMalloc(&p->rinv, sizeof(float) * std::max<int64_t>(p->sizes[SSPCG_ARRAY_RFULL], 4)));
+  SSPCG_CUDA(upload(&p->d_roff, p->offsets[SSPCG_ARRAY_RFULL]));
+  // the R blocks of problem i as the diagonal blocks of a problem with nx = nu and N - 1 block rows
+  std::vector<ProbDesc> rd(p->hdesc);
+  std::vector<int32_t> members;
+  for (int32_t i = 0; i < p->nprob; ++i) {
+    ProbDesc &d = rd[i];
+    if (d.N > 0 && d.nu > 0) members.push_back(i);
+    d.odiag = p->offsets[SSPCG_ARRAY_RFULL][i];
+    d.nx = d.nu > 0 ? d.nu : 1;
+    d.N = d.N - 1;
+    d.nu = 0;
+  }
+  SSPCG_CUDA(make_nx_groups(rd, members, p->nxg_r));
+  p->full_ready = true;
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_build_schur_full_batched(sspcg_plan *plan, const float *A, const float *B, const float *Q,
+                                            const float *R, float *D, float *E, int32_t *status,
+                                            sspcg_stream stream) {
+  if (!plan) return SSPCG_ERR_INVALID_ARG;
+  if (plan->nprob == 0) return SSPCG_OK;
+  if (!Q || !D || !status || !aligned16(Q) || !aligned16(D)) return SSPCG_ERR_INVALID_ARG;
+  if (plan->total_off > 0 && (!A || !B || !E)) return SSPCG_ERR_INVALID_ARG;
+  if (plan->sizes[SSPCG_ARRAY_RFULL] > 0 && !R) return SSPCG_ERR_INVALID_ARG;
+  sspcg_status s = full_setup(plan);
+  if (s != SSPCG_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
+  for (const NxGroup &g : plan->nxg_all)
+    SSPCG_CUDA(launch_precond_inv<float>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_refs, g.knots, g.nx,
+                                         (int)SSPCG_PRECOND_SYM_STAIR, Q, plan->qinv, status, st));
+  for (const NxGroup &g : plan->nxg_r)
+    SSPCG_CUDA(launch_precond_inv<float>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_refs, g.knots, g.nx,
+                                         (int)SSPCG_PRECOND_SYM_STAIR, R, plan->rinv, status, st));
+  SSPCG_CUDA(launch_schur_full(plan_set(plan), plan->d_kref, plan->total_knots, plan->d_roff, A, B, plan->qinv,
+                               plan->rinv, D, E, st, plan->mx));
   return SSPCG_OK;
 }
 

@@ -87,6 +87,79 @@ __global__ void __launch_bounds__(kBuildWarps * 32) schur_build_kernel(ProbSet p
 }
 
 // ---------------------------------------------------------------------------
+// K1 with full SPD cost blocks (Sec. II-A, Q_k^-1 and R_k^-1 as matrices), from
+// their inverses Qi (laid out like D) and Ri (R_{k-1}^-1 at roff[p] + (k-1) nu^2):
+//   D_0 = Q_0^-1
+//   D_k = (A_{k-1} Q_{k-1}^-1) A_{k-1}^T + (B_{k-1} R_{k-1}^-1) B_{k-1}^T + Q_k^-1
+//   E[k-1] = -A_{k-1} Q_{k-1}^-1
+// FP32; the upper triangle of D_k is summed and mirrored (Q_k^-1 is exactly
+// symmetric), so D_k is exactly symmetric.  One warp per knot.
+// Shared memory per warp: A, Q^-1, A Q^-1, B, R^-1, B R^-1 (mx*mx each).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBuildWarps * 32) schur_full_kernel(ProbSet ps, const int2 *refs,
+                                                                     int64_t total_knots, const int64_t *roff,
+                                                                     const float *__restrict__ A,
+                                                                     const float *__restrict__ B,
+                                                                     const float *__restrict__ Qi,
+                                                                     const float *__restrict__ Ri, float *D, float *E,
+                                                                     int mx) {
+  extern __shared__ float4 smem_raw[];
+  float *smem = reinterpret_cast<float *>(smem_raw);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int mm = mx * mx;
+  float *sA = smem + wid * 6 * mm, *sQ = sA + mm, *sAQ = sQ + mm, *sB = sAQ + mm, *sR = sB + mm, *sBR = sR + mm;
+  for (int64_t g = (int64_t)blockIdx.x * kBuildWarps + wid; g < total_knots; g += (int64_t)gridDim.x * kBuildWarps) {
+    const int2 ref = refs ? refs[g] : make_int2(0, (int)g);  // (problem, block row)
+    const ProbDesc d = ps.get(ref.x);
+    const int k = ref.y;
+    const int nx = d.nx, nu = d.nu, nn = nx * nx;
+    float *Dk = D + d.odiag + (int64_t)k * nn;
+    const float *Qk = Qi + d.odiag + (int64_t)k * nn;
+    if (k == 0) {
+      for (int e = lane; e < nn; e += 32) Dk[e] = Qk[e];
+      continue;
+    }
+    const float *Ak = A + d.oA + (int64_t)(k - 1) * nn;
+    const float *Bk = B + d.oB + (int64_t)(k - 1) * nx * nu;
+    const float *Qp = Qi + d.odiag + (int64_t)(k - 1) * nn;
+    const float *Rp = Ri + (roff ? roff[ref.x] : 0) + (int64_t)(k - 1) * nu * nu;
+    float *Ek = E + d.ooff + (int64_t)(k - 1) * nn;
+    for (int e = lane; e < nn; e += 32) {
+      sA[e] = Ak[e];
+      sQ[e] = Qp[e];
+    }
+    for (int e = lane; e < nx * nu; e += 32) sB[e] = Bk[e];
+    for (int e = lane; e < nu * nu; e += 32) sR[e] = Rp[e];
+    __syncwarp();
+    for (int e = lane; e < nn; e += 32) {
+      const int i = e / nx, j = e - i * nx;
+      float s = 0.0f;
+      for (int l = 0; l < nx; ++l) s = fmaf(sA[i * nx + l], sQ[l * nx + j], s);
+      sAQ[e] = s;
+      Ek[e] = -s;
+    }
+    for (int e = lane; e < nx * nu; e += 32) {
+      const int i = e / nu, j = e - i * nu;
+      float s = 0.0f;
+      for (int m = 0; m < nu; ++m) s = fmaf(sB[i * nu + m], sR[m * nu + j], s);
+      sBR[e] = s;
+    }
+    __syncwarp();
+    for (int e = lane; e < nn; e += 32) {
+      const int i = e / nx, j = e - i * nx;
+      if (i > j) continue;
+      float s = 0.0f;
+      for (int l = 0; l < nx; ++l) s = fmaf(sAQ[i * nx + l], sA[j * nx + l], s);
+      for (int m = 0; m < nu; ++m) s = fmaf(sBR[i * nu + m], sB[j * nu + m], s);
+      s += Qk[i * nx + j];
+      Dk[i * nx + j] = s;
+      Dk[j * nx + i] = s;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K2a: PD_k = D_k^-1 in FP64, one thread per knot (all knots of a launch have
 // the same nx).  GB300 issues FP64 at about 1/64 of the FP32 rate and a warp
 // instruction costs the same with any number of active lanes, so every lane
@@ -322,6 +395,23 @@ cudaError_t launch_schur_build(const ProbSet &ps, const int2 *refs, int64_t tota
   }
   schur_build_kernel<Real><<<build_grid(total_knots, sms), kBuildWarps * 32, smem, st>>>(ps, refs, total_knots,
                                                                                           A, B, qd, rd, D, E, mx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schur_full(const ProbSet &ps, const int2 *refs, int64_t total_knots, const int64_t *roff,
+                              const float *A, const float *B, const float *Qi, const float *Ri, float *D, float *E,
+                              cudaStream_t st, int mx) {
+  if (total_knots == 0) return cudaSuccess;
+  const size_t smem = sizeof(float) * kBuildWarps * 6 * mx * mx;
+  static bool attr = false;
+  if (!attr) {
+    const size_t most = sizeof(float) * kBuildWarps * 6 * kMaxNx * kMaxNx;
+    cudaError_t e = cudaFuncSetAttribute(schur_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  schur_full_kernel<<<build_grid(total_knots, 0), kBuildWarps * 32, smem, st>>>(ps, refs, total_knots, roff, A, B,
+                                                                                 Qi, Ri, D, E, mx);
   return cudaGetLastError();
 }
 

@@ -118,6 +118,11 @@ template <typename Real>
 cudaError_t launch_schur_build(const ProbSet &ps, const int2 *refs, int64_t total_knots, const float *A,
                                const float *B, const float *qd, const float *rd, Real *D, Real *E,
                                cudaStream_t st, int sms, int mx);
+// Schur blocks with full SPD cost blocks from their inverses: Qi laid out like
+// D, R_{k-1}^-1 of problem p at roff[p] + (k-1) nu^2 (roff nullptr: offset 0).
+cudaError_t launch_schur_full(const ProbSet &ps, const int2 *refs, int64_t total_knots, const int64_t *roff,
+                              const float *A, const float *B, const float *Qi, const float *Ri, float *D, float *E,
+                              cudaStream_t st, int mx);
 // Diagonal blocks of Phi^-1 (FP64 inverses), one thread per knot: every
 // knot of a launch must have the same nx.
 template <typename Real>

@@ -23,8 +23,8 @@ PRECOND = {"sym": 0, "add": 1, "bj": 2, "jacobi": 3}
 REDUCE = {"df": 0, "f32": 1, "f64": 2}
 SCHED = {"auto": 0, "resident": 1, "stream": 2}
 PRECISION = {"auto": 0, "f32": 1, "f64": 2}
-ARRAY_A, ARRAY_B, ARRAY_QD, ARRAY_RD, ARRAY_DIAG, ARRAY_OFF, ARRAY_VEC = range(7)
-NUM_ARRAYS = 7
+ARRAY_A, ARRAY_B, ARRAY_QD, ARRAY_RD, ARRAY_DIAG, ARRAY_OFF, ARRAY_VEC, ARRAY_RFULL = range(8)
+NUM_ARRAYS = 8
 MAX_NX = 28
 NOALLOC_MAX_PROBLEMS = 4096
 
@@ -93,6 +93,9 @@ def lib() -> ctypes.CDLL:
             "sspcg_plan_capture_pipeline": [_VP, _I32] + [_VP] * 14,
             "sspcg_plan_launch": [_VP, _VP],
             "sspcg_build_schur_batched": [_VP] * 8,
+            "sspcg_schur_full_work_floats": [_I32, _I32, _I32, _VP],
+            "sspcg_build_schur_full": [_I32, _I32, _I32] + [_VP] * 9,
+            "sspcg_build_schur_full_batched": [_VP] * 9,
             "sspcg_build_precond_batched": [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP],
             "sspcg_solve_batched": [_VP] * 11,
             "sspcg_solve_qp_batched": [_VP] * 13,
@@ -305,6 +308,24 @@ plan_stats = sspcg_plan_stats
 def sspcg_build_schur_batched(plan: Plan, A, B, qd, rd, D, E, stream=None):
     _check(lib().sspcg_build_schur_batched(plan.handle, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(D), _ptr(E),
                                            _stream(stream)), "sspcg_build_schur_batched")
+
+
+def sspcg_schur_full_work_floats(N, nx, nu) -> int:
+    out = ctypes.c_int64(0)
+    _check(lib().sspcg_schur_full_work_floats(N, nx, nu, ctypes.byref(out)), "sspcg_schur_full_work_floats")
+    return int(out.value)
+
+
+def sspcg_build_schur_full(N, nx, nu, A, B, Q, R, D, E, work, status, stream=None):
+    """Schur blocks from full SPD Q_k, R_k (Sec. II-A); status: device int32[1]."""
+    _check(lib().sspcg_build_schur_full(N, nx, nu, _ptr(A), _ptr(B), _ptr(Q), _ptr(R), _ptr(D), _ptr(E), _ptr(work),
+                                        _ptr(status), _stream(stream)), "sspcg_build_schur_full")
+
+
+def sspcg_build_schur_full_batched(plan: Plan, A, B, Q, R, D, E, status, stream=None):
+    """Batched full-cost Schur build: Q packed like D (ARRAY_DIAG), R in ARRAY_RFULL."""
+    _check(lib().sspcg_build_schur_full_batched(plan.handle, _ptr(A), _ptr(B), _ptr(Q), _ptr(R), _ptr(D), _ptr(E),
+                                                _ptr(status), _stream(stream)), "sspcg_build_schur_full_batched")
 
 
 def sspcg_build_precond_batched(plan: Plan, kind, D, E, PD, PE, status, stream=None):

@@ -67,6 +67,17 @@ def test_invalid_shapes_rejected_on_host(L):
     assert L.sspcg_plan_destroy(None) == sspcg.ERR_INVALID_ARG
 
 
+def test_full_cost_work_size_on_host(L):
+    from paper_2309_06427_gb300 import sspcg
+    out = ctypes.c_int64(-1)
+    # (N+1) nx^2 rounded up to 4, then N nu^2: 5 * 9 -> 48, + 4 * 4
+    assert L.sspcg_schur_full_work_floats(4, 3, 2, ctypes.byref(out)) == sspcg.OK and out.value == 64
+    assert L.sspcg_schur_full_work_floats(4, 29, 2, ctypes.byref(out)) == sspcg.ERR_INVALID_ARG
+    vp = ctypes.c_void_p(16)
+    # missing work buffer: rejected before any CUDA call
+    assert L.sspcg_build_schur_full(4, 3, 2, vp, vp, vp, vp, vp, vp, None, vp, None) == sspcg.ERR_INVALID_ARG
+
+
 def test_product_code_never_imports_the_oracle():
     pkg = os.path.join(ROOT, "paper_2309_06427_gb300")
     for dirpath, _, files in os.walk(pkg):
