@@ -2,6 +2,7 @@
 // Sec. III, Sec. IV, Eq. jacobi).  One warp per knot; the batch is a flat
 // list of knots whose (problem, block row) pairs the plan tabulates.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -160,18 +161,16 @@ __global__ void __launch_bounds__(kBuildWarps * 32) schur_full_kernel(ProbSet ps
 }
 
 // ---------------------------------------------------------------------------
-// K2a: PD_k = D_k^-1 in FP64, one thread per knot (all knots of a launch have
-// the same nx).  GB300 issues FP64 at about 1/64 of the FP32 rate and a warp
-// instruction costs the same with any number of active lanes, so every lane
-// works on a knot of its own.  Per thread, in shared memory: the lower
-// triangle of D_k (row stride nx, odd total stride per thread for
-// conflict-free 8-byte accesses).
-//   LDL^T, right-looking, rows updated from the bottom so that column j stays
-//   unscaled until its row is done:            nx^3/6 FMA
-//   L^-1 in place (unit lower), column by column:  nx^3/6 FMA
+// K2a: PD_k = D_k^-1 by LDL^T in FP64 (FP64 output) or double-float (FP32
+// output: about 48 bits on the FP32 units; GB300 issues FP64 at about 1/64 of
+// the FP32 rate), G lanes per knot (all knots of a launch have the same nx).
+// In shared memory per knot: the packed lower triangle of D_k (8-byte entries,
+// odd stride for conflict-free accesses).
+//   LDL^T, right-looking:                               nx^3/6 FMA
+//   L^-1 in place (unit lower), row by row:             nx^3/6 FMA
 //   D^-1(i,j) = sum_{t>=i} W(t,i) (1/d_t) W(t,j), i >= j:  nx^3/6 FMA
-// Reciprocals: FP32 reciprocal refined by two FP64 Newton steps
-// (2^-23 -> 2^-46 -> below 2^-53).  Jacobi: PD_k = diag(1 / D_k(i,i)).
+// Reciprocals: FP32 reciprocal refined by Newton steps (two in FP64, one in
+// double-float).  Jacobi: PD_k = diag(1 / D_k(i,i)).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double rcp_f64(double x) {
   double y = (double)(1.0f / (float)x);
@@ -194,10 +193,44 @@ __device__ __forceinline__ int tri(int i, int c) { return i * (i + 1) / 2 + c; }
 // loops and synchronise with __syncwarp over the warp's active lanes.  Every
 // entry is computed with the same operations in the same order as one lane
 // would, so the result does not depend on G.
+// Arithmetic of the inversion: FP64 for the FP64 path (FP64 output), double-float for FP32 output (about 48
+// bits on the FP32 units, which run at about 60x the FP64 rate; the output is rounded to FP32 once).  Both
+// run the same operations in the same order.
+template <typename T> struct InvArith;
+template <> struct InvArith<double> {
+  using T = double;
+  static __device__ __forceinline__ T from(double v) { return v; }
+  static __device__ __forceinline__ T fnma(T a, T b, T c) { return fma(-a, b, c); }  // c - a b
+  static __device__ __forceinline__ T fma3(T a, T b, T c) { return fma(a, b, c); }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T neg(T a) { return -a; }
+  static __device__ __forceinline__ T rcp(T a) { return rcp_f64(a); }
+  static __device__ __forceinline__ T sqrt_(T a) { return sqrt(a); }
+  static __device__ __forceinline__ bool pos_finite(T a) { return a > 0.0 && isfinite(a); }
+  template <typename Real> static __device__ __forceinline__ Real out(T a) { return (Real)a; }
+};
+template <> struct InvArith<df> {
+  using T = df;
+  static __device__ __forceinline__ T from(float v) { return {v, 0.0f}; }
+  static __device__ __forceinline__ T fnma(T a, T b, T c) { return df_fma3(df_neg(a), b, c); }
+  static __device__ __forceinline__ T fma3(T a, T b, T c) { return df_fma3(a, b, c); }
+  static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+  static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+  static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
+  static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
+  static __device__ __forceinline__ T sqrt_(T a) { return df_sqrt(a); }
+  static __device__ __forceinline__ bool pos_finite(T a) { return a.hi > 0.0f && isfinite(a.hi); }
+  template <typename Real> static __device__ __forceinline__ Real out(T a) { return (Real)__fadd_rn(a.hi, a.lo); }
+};
+
 template <typename Real, int G>
 __global__ void __launch_bounds__(512, 1) precond_inv_kernel(ProbSet ps, const int2 *refs, int64_t total_knots, int nx,
                                                           int kind, const Real *__restrict__ D, Real *PD,
                                                           int32_t *status) {
+  using A = InvArith<typename std::conditional<sizeof(Real) == sizeof(float), df, double>::type>;
+  using T = typename A::T;
+  static_assert(sizeof(T) == sizeof(double), "8-byte entries: the shared-memory layout is the same for both");
   extern __shared__ double dsm[];
   const int lg = threadIdx.x % G, grp = threadIdx.x / G;
   const int64_t g = (int64_t)blockIdx.x * (blockDim.x / G) + grp;
@@ -222,41 +255,41 @@ __global__ void __launch_bounds__(512, 1) precond_inv_kernel(ProbSet ps, const i
     if (bad) status[d.id] = kNotSpd;
     return;
   }
-  double *M = dsm + (int64_t)grp * (inv_stride(nx) + nx);
-  double *tmp = M + inv_stride(nx);
+  T *M = reinterpret_cast<T *>(dsm) + (int64_t)grp * (inv_stride(nx) + nx);
+  T *tmp = M + inv_stride(nx);
   for (int i = 0; i < nx; ++i)
-    for (int c = lg; c <= i; c += G) M[tri(i, c)] = (double)Dk[i * nx + c];
+    for (int c = lg; c <= i; c += G) M[tri(i, c)] = A::from(Dk[i * nx + c]);
   __syncwarp(mask);
   // LDL^T: after step j, M(j,j) = 1/d_j and M(i,j) = L(i,j) for i > j.  Rows i > j are split cyclically.
   bool bad = false;
   for (int j = 0; j < nx; ++j) {
-    const double djj = M[tri(j, j)];
-    bad |= !(djj > 0.0) || !isfinite(djj);
-    const double inv = rcp_f64(djj);
+    const T djj = M[tri(j, j)];
+    bad |= !A::pos_finite(djj);
+    const T inv = A::rcp(djj);
     for (int i = j + 1 + lg; i < nx; i += G) {
-      double *Mi = M + tri(i, 0);
-      const double lij = Mi[j] * inv;
+      T *Mi = M + tri(i, 0);
+      const T lij = A::mul(Mi[j], inv);
 #pragma unroll 4
-      for (int c = j + 1; c <= i; ++c) Mi[c] = fma(-lij, M[tri(c, j)], Mi[c]);
+      for (int c = j + 1; c <= i; ++c) Mi[c] = A::fnma(lij, M[tri(c, j)], Mi[c]);
     }
     __syncwarp(mask);  // column j no longer read
-    for (int i = j + 1 + lg; i < nx; i += G) M[tri(i, j)] = M[tri(i, j)] * inv;
+    for (int i = j + 1 + lg; i < nx; i += G) M[tri(i, j)] = A::mul(M[tri(i, j)], inv);
     if (lg == 0) M[tri(j, j)] = inv;
     __syncwarp(mask);
   }
   // W = L^-1 (unit lower) in place, row by row; the columns of a row are split cyclically.
   //   W(i,j) = -(L(i,j) + sum_{j<t<i} L(i,t) W(t,j))
   for (int i = 1; i < nx; ++i) {
-    const double *Mi = M + tri(i, 0);
+    const T *Mi = M + tri(i, 0);
     for (int j = lg; j < i; j += G) {
-      double s0 = Mi[j], s1 = 0.0;  // two chains
+      T s0 = Mi[j], s1 = A::from(0.0f);  // two chains
       int t = j + 1;
       for (; t + 1 < i; t += 2) {
-        s0 = fma(Mi[t], M[tri(t, j)], s0);
-        s1 = fma(Mi[t + 1], M[tri(t + 1, j)], s1);
+        s0 = A::fma3(Mi[t], M[tri(t, j)], s0);
+        s1 = A::fma3(Mi[t + 1], M[tri(t + 1, j)], s1);
       }
-      if (t < i) s0 = fma(Mi[t], M[tri(t, j)], s0);
-      tmp[j] = -(s0 + s1);
+      if (t < i) s0 = A::fma3(Mi[t], M[tri(t, j)], s0);
+      tmp[j] = A::neg(A::add(s0, s1));
     }
     __syncwarp(mask);  // row i's L entries no longer read
     for (int j = lg; j < i; j += G) M[tri(i, j)] = tmp[j];
@@ -268,9 +301,9 @@ __global__ void __launch_bounds__(512, 1) precond_inv_kernel(ProbSet ps, const i
   constexpr bool kVtV = sizeof(Real) == sizeof(float);
   if (kVtV && !bad) {
     for (int t = lg; t < nx; t += G) {
-      double *Mt = M + tri(t, 0);
-      const double sc = sqrt(Mt[t]);
-      for (int c = 0; c < t; ++c) Mt[c] *= sc;
+      T *Mt = M + tri(t, 0);
+      const T sc = A::sqrt_(Mt[t]);
+      for (int c = 0; c < t; ++c) Mt[c] = A::mul(Mt[c], sc);
       Mt[t] = sc;
     }
   }
@@ -287,32 +320,32 @@ __global__ void __launch_bounds__(512, 1) precond_inv_kernel(ProbSet ps, const i
     while (tri(i + 1, 0) <= e) ++i;
     while (tri(i, 0) > e) --i;
     const int j = e - tri(i, 0);
-    double s0, s1 = 0.0;  // two chains
+    T s0, s1 = A::from(0.0f);  // two chains
     int t = i + 1;
     if constexpr (kVtV) {
-      s0 = M[tri(i, i)] * M[tri(i, j)];
+      s0 = A::mul(M[tri(i, i)], M[tri(i, j)]);
       for (; t + 1 < nx; t += 2) {
-        const double *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
-        s0 = fma(Mt[i], Mt[j], s0);
-        s1 = fma(Mu[i], Mu[j], s1);
+        const T *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
+        s0 = A::fma3(Mt[i], Mt[j], s0);
+        s1 = A::fma3(Mu[i], Mu[j], s1);
       }
       if (t < nx) {
-        const double *Mt = M + tri(t, 0);
-        s0 = fma(Mt[i], Mt[j], s0);
+        const T *Mt = M + tri(t, 0);
+        s0 = A::fma3(Mt[i], Mt[j], s0);
       }
     } else {
-      s0 = M[tri(i, i)] * (i == j ? 1.0 : M[tri(i, j)]);
+      s0 = A::mul(M[tri(i, i)], i == j ? A::from(1.0f) : M[tri(i, j)]);
       for (; t + 1 < nx; t += 2) {
-        const double *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
-        s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
-        s1 = fma(Mu[i] * Mu[t + 1], Mu[j], s1);
+        const T *Mt = M + tri(t, 0), *Mu = M + tri(t + 1, 0);
+        s0 = A::fma3(A::mul(Mt[i], Mt[t]), Mt[j], s0);
+        s1 = A::fma3(A::mul(Mu[i], Mu[t + 1]), Mu[j], s1);
       }
       if (t < nx) {
-        const double *Mt = M + tri(t, 0);
-        s0 = fma(Mt[i] * Mt[t], Mt[j], s0);
+        const T *Mt = M + tri(t, 0);
+        s0 = A::fma3(A::mul(Mt[i], Mt[t]), Mt[j], s0);
       }
     }
-    const Real f = (Real)(s0 + s1);
+    const Real f = A::template out<Real>(A::add(s0, s1));
     PDk[i * nx + j] = f;
     PDk[j * nx + i] = f;
   }

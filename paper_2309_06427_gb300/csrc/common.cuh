@@ -90,6 +90,45 @@ __device__ __forceinline__ df warp_sum(df v) {
 
 __device__ __forceinline__ double df_to_double(df v) { return (double)v.hi + (double)v.lo; }
 
+// Products of double-float values: the exact product of the high parts (one
+// FMA gives its error) plus the cross terms; the lo * lo term is below the
+// format's precision.
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+// c + a * b for double-float a, b, c.
+__device__ __forceinline__ df df_fma3(df a, df b, df c) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  df s = two_sum(c.hi, p);
+  float e = __fadd_rn(s.lo, __fadd_rn(c.lo, pe));
+  return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+// 1 / x: the FP32 reciprocal and one Newton step y + y (1 - x y) with the
+// residual formed in double-float (about 46 bits).
+__device__ __forceinline__ df df_rcp(df x) {
+  const float y = __frcp_rn(x.hi);
+  const df r = df_fma3(df_neg(x), df{y, 0.0f}, df{1.0f, 0.0f});  // 1 - x y
+  return fast_two_sum(y, __fmul_rn(y, r.hi));
+}
+
+// sqrt(x), x > 0: the FP32 square root and one Newton step s + (x - s^2) / (2 s).
+__device__ __forceinline__ df df_sqrt(df x) {
+  const float s = __fsqrt_rn(x.hi);
+  const df r = df_fma3(df{-s, 0.0f}, df{s, 0.0f}, x);  // x - s^2
+  return fast_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.0f, s)));
+}
+
 // Ceil-div helpers.
 __host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
