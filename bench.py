@@ -82,7 +82,9 @@ def parse():
     ap.add_argument("--no-paper-stats", action="store_true",
                     help="skip the Fig. 1-3 statistics (spectra and iterations per preconditioner)")
     ap.add_argument("--train-problems", type=int, default=4096, help="training problems of the warm-start network")
-    ap.add_argument("--train-epochs", type=int, default=6)
+    ap.add_argument("--train-epochs", type=int, default=1)
+    ap.add_argument("--train-gammas", type=int, default=49,
+                    help="right-hand sides per training problem (its own gamma and seeded N(0, 1) draws)")
     ap.add_argument("--mpc", action="store_true",
                     help="add the MPC batch (16384 problems, 10 sequential re-solves, plain vs warm-started)")
     ap.add_argument("--mpc-resolves", type=int, default=10)
@@ -229,7 +231,9 @@ def run_reference(args, world, rank):
 
 def train_warm_start(args, torch, sspcg, rank):
     """Train the warm-start network (untimed) on plain solves of the manipulator-like and ragged-batch
-    generators; returns the network and its loss history."""
+    generators: ``--train-problems`` problems, each solved for its own gamma and for ``--train-gammas`` - 1
+    more seeded N(0, 1) right-hand sides (4096 x 49 = 200,704 solves by default); returns the network, its
+    loss history and the number of solves."""
     half = max(1, args.train_problems // 2)
     base = (1 << 20) + rank * args.train_problems  # disjoint from every rank's benchmark problems
     train = [P.make_problem(P.config_key(2, base + i), 64, 14, 7, 0.01) for i in range(half)]
@@ -242,18 +246,31 @@ def train_warm_start(args, torch, sspcg, rank):
     net = sspcg.sspcg_mlp_create(MLP_MAX_ROWS)
     sspcg.sspcg_mlp_fit_normalisation(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD)
     sspcg.sspcg_mlp_set_params(net, torch.from_numpy(P.mlp_initial_params(0)).cuda())
+    # right-hand sides: the problems' own gamma, then seeded N(0, 1) draws; lambda* of each by the batched PCG
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1 << 40)
+    gammas, lams = [d["gamma"]], [b.lam.clone()]
+    it = torch.zeros_like(b.iters); rr = torch.zeros_like(b.relres); st = torch.zeros_like(b.status)
+    for _ in range(1, max(1, args.train_gammas)):
+        g = torch.randn(d["gamma"].shape, generator=gen, device="cuda", dtype=torch.float32)
+        lam = torch.zeros_like(g)
+        sspcg.sspcg_solve_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE, g, lam, it, rr, st)
+        gammas.append(g)
+        lams.append(lam)
+    torch.cuda.synchronize()
     chunk = 32
     starts = list(range(0, plan.nprob, chunk))
+    pairs = [(r, s0) for r in range(len(gammas)) for s0 in starts]
     rng = np.random.default_rng(0)
-    loss = torch.zeros(len(starts), dtype=torch.float64, device="cuda")
-    lam_star = b.lam.clone()
+    loss = torch.zeros(len(pairs), dtype=torch.float64, device="cuda")
     hist = []
     for _ in range(args.train_epochs):
-        for j, s0 in enumerate(rng.permutation(starts)):
+        for j in rng.permutation(len(pairs)):
+            r, s0 = pairs[j]
             sspcg.sspcg_mlp_train_step(net, plan, int(s0), min(int(s0) + chunk, plan.nprob), d["A"], d["B"], d["qd"],
-                                       d["rd"], d["gamma"], b.D, b.E, b.PD, lam_star, sspcg.adam(), loss[j:j + 1])
+                                       d["rd"], gammas[r], b.D, b.E, b.PD, lams[r], sspcg.adam(), loss[j:j + 1])
         hist.append(float(loss.mean().item()))
-    return net, hist, len(train)
+    return net, hist, len(train) * len(gammas)
 
 
 def warm_start_comparison(args, torch, sspcg, stream, rank):
@@ -319,7 +336,8 @@ def warm_start_comparison(args, torch, sspcg, stream, rank):
     # plain steps in lanes; warm steps: the two-half pipeline plus, per chunk of MLP_MAX_ROWS rows, features,
     # three products and the scatter
     chunks = -(-sum(p.n for p in probs) // MLP_MAX_ROWS)
-    return {"workload": w.name, "train_problems": ntrain, "train_epochs": args.train_epochs,
+    return {"workload": w.name, "train_problems": args.train_problems, "train_solves": ntrain,
+            "train_epochs": args.train_epochs,
             "train_loss": [round(x, 4) for x in hist], "train_seconds": round(train_s, 2),
             "plain": out["plain"], "warm": out["warm"],
             "inference": {"rows": rows, "flop_per_row": MLP_FLOP_PER_ROW, **infer},

@@ -461,6 +461,8 @@ sspcg_status sspcg_solve_qp_batched_noalloc(int32_t nprob, const int32_t *N, con
  * The problem tables (shapes, packed offsets) come from a plan; every array
  * argument is a device pointer in the plan's packed layout.  A network object
  * owns its parameters, Adam state and the workspace of max_rows knot rows.
+ * The layout holds nu <= 14: calls on a plan with a larger nu return
+ * SSPCG_ERR_UNSUPPORTED.
  */
 #define SSPCG_MLP_IN 1344
 #define SSPCG_MLP_HIDDEN 256

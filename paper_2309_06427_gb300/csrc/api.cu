@@ -1286,6 +1286,8 @@ PlanView plan_view(const sspcg_plan *p) {
   v.knot_start = p->knot_start.data();
   v.d_knot_start = p->d_knot_start;
   v.total_off = p->total_off;
+  v.max_nu = 0;
+  for (const ProbDesc &d : p->hdesc) v.max_nu = std::max(v.max_nu, d.nu);
   return v;
 }
 sspcg_status build_half(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B, const float *qd,

@@ -18,6 +18,7 @@ struct PlanView {
   const int64_t *knot_start;    // host: first knot of each problem, nprob + 1 entries
   const int64_t *d_knot_start;  // the same on the device
   int64_t total_off;            // number of off-diagonal blocks
+  int32_t max_nu;               // largest nu of the batch
 };
 
 int sms();

@@ -36,8 +36,12 @@ struct QpData {
   const float *A, *B, *qd, *rd, *gamma, *PD;
 };
 
-cudaError_t launch_features(const RowSpan &rs, const QpData &q, const float *mu, const float *isd, bf16 *X,
-                            cudaStream_t st);
+// Gather table of the feature columns for every (nx <= 28, nu <= 14): kFeatTable int16 entries (host).
+constexpr int64_t kFeatTable = (int64_t)kPadX * (kPadU + 1) * kIn;
+void build_feature_table(int16_t *tab);
+// Normalised bf16 feature rows of the span into X; tab: the gather table on the device.
+cudaError_t launch_features(const RowSpan &rs, const QpData &q, const float *mu, const float *isd,
+                            const int16_t *tab, bf16 *X, cudaStream_t st);
 // Column sums of the raw features over the span: part [warps][2][kIn] (FP64); returns warps used.
 cudaError_t launch_feature_stats(const RowSpan &rs, const QpData &q, double *part, int warps, cudaStream_t st);
 cudaError_t launch_stats_finish(const double *part, int warps, int64_t rows, float *mu, float *isd,

@@ -19,6 +19,7 @@ struct sspcg_mlp {
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 [kParams]
   bf16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr, *W2t = nullptr, *W3t = nullptr;
   float *mu = nullptr, *isd = nullptr;  // [kIn]
+  int16_t *ftab = nullptr;              // feature gather table [kFeatTable]
   int64_t t = 0;                        // Adam steps taken
   // workspace for max_rows rows
   bf16 *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dY = nullptr, *dH2 = nullptr, *dH1 = nullptr;
@@ -44,7 +45,8 @@ void mlp_free(sspcg_mlp *n) {
   for (void *p : {(void *)n->w, (void *)n->g, (void *)n->m, (void *)n->v, (void *)n->W1b, (void *)n->W2b,
                   (void *)n->W3b, (void *)n->W2t, (void *)n->W3t, (void *)n->mu, (void *)n->isd, (void *)n->X,
                   (void *)n->H1, (void *)n->H2, (void *)n->dY, (void *)n->dH2, (void *)n->dH1, (void *)n->Y,
-                  (void *)n->U, (void *)n->uu, (void *)n->gg, (void *)n->part, (void *)n->stat_part, (void *)n->err})
+                  (void *)n->U, (void *)n->uu, (void *)n->gg, (void *)n->part, (void *)n->stat_part, (void *)n->err,
+                  (void *)n->ftab})
     cudaFree(p);
   delete n;
 }
@@ -54,6 +56,9 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 QpData qp(const float *A, const float *B, const float *qd, const float *rd, const float *gamma, const float *PD) {
   return QpData{A, B, qd, rd, gamma, PD};
 }
+
+// The feature layout pads A_k to 28 x 28 and B_k to 28 x 14: batches with nu > 14 are not supported.
+bool layout_fits(const host::PlanView &v) { return v.max_nu <= kPadU; }
 
 bool qp_ok(const host::PlanView &v, const float *A, const float *B, const float *qd, const float *rd,
            const float *gamma, const float *PD) {
@@ -78,7 +83,7 @@ sspcg_status refresh_copies(sspcg_mlp *n, cudaStream_t st) {
 sspcg_status forward(sspcg_mlp *n, const host::PlanView &v, int64_t row0, int64_t rows, const QpData &q,
                      cudaStream_t st) {
   RowSpan rs{v.ps, v.kref, row0, rows};
-  MLP_CUDA(launch_features(rs, q, n->mu, n->isd, n->X, st));
+  MLP_CUDA(launch_features(rs, q, n->mu, n->isd, n->ftab, n->X, st));
   if (n->engine == SSPCG_MLP_ENGINE_TCGEN05) {
     MLP_CUDA(launch_gemm_nt_tc(kEpiBiasRelu, n->X, n->W1b, rows, kHid, kIn, n->w + kB1, n->H1, nullptr, n->err, st));
     MLP_CUDA(launch_gemm_nt_tc(kEpiBiasRelu, n->H1, n->W2b, rows, kHid, kHid, n->w + kB2, n->H2, nullptr, n->err, st));
@@ -127,7 +132,14 @@ sspcg_status sspcg_mlp_create(sspcg_mlp **out, int32_t max_rows) {
   alloc(&n->uu, R); alloc(&n->gg, R);
   alloc(&n->part, part_floats(R));
   alloc(&n->err, 1);
+  alloc(&n->ftab, kFeatTable);
   if (e != cudaSuccess) return fail(e);
+  {
+    std::vector<int16_t> tab(kFeatTable);
+    build_feature_table(tab.data());
+    if ((e = cudaMemcpy(n->ftab, tab.data(), sizeof(int16_t) * kFeatTable, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(e);
+  }
   if ((e = cudaMemset(n->err, 0, sizeof(int))) != cudaSuccess) return fail(e);
   if (!tc_available()) n->engine = SSPCG_MLP_ENGINE_MMA_SYNC;
   for (float *p : {n->w, n->g, n->m, n->v})
@@ -209,6 +221,7 @@ sspcg_status sspcg_mlp_fit_normalisation(sspcg_mlp *n, const sspcg_plan *plan, c
   const host::PlanView v = host::plan_view(plan);
   if (v.nprob == 0) return SSPCG_OK;
   if (!qp_ok(v, A, B, qd, rd, gamma, PD)) return SSPCG_ERR_INVALID_ARG;
+  if (!layout_fits(v)) return SSPCG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   const int warps = feature_stats_warps(host::sms());
   if (n->stat_warps < warps) {
@@ -232,10 +245,11 @@ sspcg_status sspcg_mlp_features(const sspcg_mlp *n, const sspcg_plan *plan, int3
   if (p_begin < 0 || p_end > v.nprob || p_begin > p_end) return SSPCG_ERR_INVALID_ARG;
   if (p_begin == p_end) return SSPCG_OK;
   if (!qp_ok(v, A, B, qd, rd, gamma, PD)) return SSPCG_ERR_INVALID_ARG;
+  if (!layout_fits(v)) return SSPCG_ERR_UNSUPPORTED;
   const int64_t row0 = v.knot_start[p_begin], rows = v.knot_start[p_end] - row0;
   if (rows > n->max_rows) return SSPCG_ERR_INVALID_ARG;
   RowSpan rs{v.ps, v.kref, row0, rows};
-  MLP_CUDA(launch_features(rs, qp(A, B, qd, rd, gamma, PD), n->mu, n->isd, reinterpret_cast<bf16 *>(X),
+  MLP_CUDA(launch_features(rs, qp(A, B, qd, rd, gamma, PD), n->mu, n->isd, n->ftab, reinterpret_cast<bf16 *>(X),
                            (cudaStream_t)stream));
   return SSPCG_OK;
 }
@@ -247,6 +261,7 @@ sspcg_status sspcg_mlp_infer(sspcg_mlp *n, const sspcg_plan *plan, const float *
   const host::PlanView v = host::plan_view(plan);
   if (v.nprob == 0) return SSPCG_OK;
   if (!qp_ok(v, A, B, qd, rd, gamma, PD)) return SSPCG_ERR_INVALID_ARG;
+  if (!layout_fits(v)) return SSPCG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   const QpData q = qp(A, B, qd, rd, gamma, PD);
   for (int64_t r0 = 0; r0 < v.knots; r0 += n->max_rows) {
@@ -267,6 +282,7 @@ sspcg_status sspcg_mlp_train_step(sspcg_mlp *n, const sspcg_plan *plan, int32_t 
   const host::PlanView v = host::plan_view(plan);
   if (p_begin < 0 || p_end > v.nprob || p_begin >= p_end) return SSPCG_ERR_INVALID_ARG;
   if (!qp_ok(v, A, B, qd, rd, gamma, PD) || (v.total_off > 0 && !E)) return SSPCG_ERR_INVALID_ARG;
+  if (!layout_fits(v)) return SSPCG_ERR_UNSUPPORTED;
   if (!(hyper->lr >= 0.f) || !(hyper->beta1 >= 0.f && hyper->beta1 < 1.f) ||
       !(hyper->beta2 >= 0.f && hyper->beta2 < 1.f) || !(hyper->eps > 0.f))
     return SSPCG_ERR_INVALID_ARG;
@@ -314,6 +330,7 @@ sspcg_status sspcg_pipeline_warm_batched(sspcg_plan *plan, sspcg_mlp *n, sspcg_p
       (v.total_off > 0 && (!E || !PE)))
     return SSPCG_ERR_INVALID_ARG;
   if (!aligned16(qd) || !aligned16(D)) return SSPCG_ERR_INVALID_ARG;
+  if (!layout_fits(v)) return SSPCG_ERR_UNSUPPORTED;
   sspcg_status s = host::build_half(plan, kind, A, B, qd, rd, D, E, PD, PE, status, stream);
   if (s != SSPCG_OK) return s;
   if ((s = sspcg_mlp_infer(n, plan, A, B, qd, rd, gamma, PD, lambda, stream)) != SSPCG_OK) return s;

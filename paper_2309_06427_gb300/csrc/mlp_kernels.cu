@@ -17,7 +17,8 @@ namespace {
 // (all segment starts and the row lengths 28 and 14 are even).
 // ---------------------------------------------------------------------------
 constexpr int kStA = 0, kStB = 784, kStPD = 1176, kStQp = 1960, kStRp = 1988, kStQ = 2002, kStG = 2030;
-constexpr int kStFloats = 2064;  // per warp (8,256 bytes)
+constexpr int kStDj = 2058, kStNx = 2086, kStZero = 2087;  // D_k^-1 gamma_k, nx / 28, a zero
+constexpr int kStFloats = 2088;  // per warp (8,352 bytes)
 constexpr int kFeatWarps = 4;
 
 // dst[i] = src[i] for i < n <= MAXN: all loads issued before the stores.
@@ -110,9 +111,47 @@ __device__ __forceinline__ float block_solve(const float *s, int m, int lane) {
 
 constexpr int kPairIters = kIn / 64;  // 21 column pairs per lane
 
-// One warp per knot row; lane l writes columns 64 i + 2 l, +1.
+}  // namespace
+
+// Gather table of the feature columns: for every (nx, nu) with nu <= 14, the stage index each column
+// reads (kStZero for padding), in the column layout of feature_pair.
+void build_feature_table(int16_t *tab) {
+  for (int m = 1; m <= kPadX; ++m)
+    for (int u = 0; u <= kPadU; ++u) {
+      int16_t *t = tab + ((int64_t)(m - 1) * (kPadU + 1) + u) * kIn;
+      for (int c = 0; c < kIn; ++c) {
+        int idx = kStZero;
+        if (c < kOffB) {
+          const int i = c / kPadX, j = c % kPadX;
+          if (i < m && j < m) idx = kStA + i * m + j;
+        } else if (c < kOffQp) {
+          const int cc = c - kOffB, i = cc / kPadU, j = cc % kPadU;
+          if (i < m && j < u) idx = kStB + i * u + j;
+        } else if (c < kOffRp) {
+          if (c - kOffQp < m) idx = kStQp + (c - kOffQp);
+        } else if (c < kOffQ) {
+          if (c - kOffRp < u) idx = kStRp + (c - kOffRp);
+        } else if (c < kOffG) {
+          if (c - kOffQ < m) idx = kStQ + (c - kOffQ);
+        } else if (c < kOffDj) {
+          if (c - kOffG < m) idx = kStG + (c - kOffG);
+        } else if (c < kOffNx) {
+          if (c - kOffDj < m) idx = kStDj + (c - kOffDj);
+        } else if (c == kOffNx) {
+          idx = kStNx;
+        }
+        t[c] = (int16_t)idx;
+      }
+    }
+}
+
+namespace {
+
+// One warp per knot row: stage the knot's data (zeros for the k - 1 blocks of row 0), then lane l writes
+// columns 64 i + 2 l, +1, each gathered from the stage through the table of the problem's (nx, nu).
 __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(RowSpan rs, QpData q, const float *__restrict__ mu,
                                                                    const float *__restrict__ isd,
+                                                                   const int16_t *__restrict__ tab,
                                                                    bf16 *__restrict__ X) {
   __shared__ __align__(16) float stage[kFeatWarps][kStFloats];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -122,22 +161,31 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(RowSpan rs, Q
   const ProbDesc d = rs.ps.get(ref.x);
   const int k = ref.y, m = d.nx, u = d.nu;
   float *s = stage[wl];
-  stage_knot(s, d, k, q, lane);
-  const float dj = block_solve(s, m, lane);
+  if (k == 0) {  // no A_{k-1}, B_{k-1}, diag Q_{k-1}, diag R_{k-1}: their columns read zeros
+    for (int e = lane; e < m * m; e += 32) s[kStA + e] = 0.f;
+    for (int e = lane; e < m * u; e += 32) s[kStB + e] = 0.f;
+    if (lane < m) s[kStQp + lane] = 0.f;
+    if (lane < u) s[kStRp + lane] = 0.f;
+  }
+  stage_knot(s, d, k, q, lane);  // ends with __syncwarp
+  const float dj = block_solve(s, m, lane);  // zero for lane >= nx
+  if (lane < kPadX) s[kStDj + lane] = dj;
+  if (lane == 0) {
+    s[kStNx] = (float)m / (float)kPadX;
+    s[kStZero] = 0.f;
+  }
+  __syncwarp();
+  const int16_t *t = tab + ((int64_t)(m - 1) * (kPadU + 1) + u) * kIn;
   __nv_bfloat162 *out = reinterpret_cast<__nv_bfloat162 *>(X + r * kIn);
 #pragma unroll
   for (int it = 0; it < kPairIters; ++it) {
     const int c = it * 64 + 2 * lane;
-    float dj0 = 0.f, dj1 = 0.f;
-    if (it >= kOffDj / 64) {  // iterations that may cover the D^-1 gamma slot
-      const int sidx = min(max(c - kOffDj, 0), 30);
-      dj0 = __shfl_sync(0xffffffffu, dj, sidx);
-      dj1 = __shfl_sync(0xffffffffu, dj, sidx + 1);
-    }
-    float2 v = feature_pair(c, m, u, k, s, dj0, dj1);
-    v.x = (v.x - mu[c]) * isd[c];
-    v.y = (v.y - mu[c + 1]) * isd[c + 1];
-    out[c >> 1] = __floats2bfloat162_rn(v.x, v.y);
+    const short2 id = *reinterpret_cast<const short2 *>(t + c);
+    const float2 mm = *reinterpret_cast<const float2 *>(mu + c);
+    const float2 is = *reinterpret_cast<const float2 *>(isd + c);
+    const float vx = (s[id.x] - mm.x) * is.x;
+    const float vy = (s[id.y] - mm.y) * is.y;
+    out[c >> 1] = __floats2bfloat162_rn(vx, vy);
   }
 }
 
@@ -579,10 +627,10 @@ int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace
 
-cudaError_t launch_features(const RowSpan &rs, const QpData &q, const float *mu, const float *isd, bf16 *X,
-                            cudaStream_t st) {
+cudaError_t launch_features(const RowSpan &rs, const QpData &q, const float *mu, const float *isd,
+                            const int16_t *tab, bf16 *X, cudaStream_t st) {
   if (rs.nrows <= 0) return cudaSuccess;
-  features_kernel<<<(unsigned)cdiv64(rs.nrows, kFeatWarps), kFeatWarps * 32, 0, st>>>(rs, q, mu, isd, X);
+  features_kernel<<<(unsigned)cdiv64(rs.nrows, kFeatWarps), kFeatWarps * 32, 0, st>>>(rs, q, mu, isd, tab, X);
   return cudaGetLastError();
 }
 
