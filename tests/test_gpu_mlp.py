@@ -238,6 +238,21 @@ def test_invalid_arguments():
         sspcg.sspcg_mlp_create(0)
 
 
+def test_inputs_wider_than_the_feature_layout_are_unsupported():
+    """The layout pads B_k to 28 x 14: a batch with nu = 15 is refused on the host, before any kernel."""
+    probs = P.custom_problems([(6, 20, 15), (4, 5, 3)], config=85)
+    plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
+                                   sspcg.options(tol=1e-6))
+    b = sspcg.Batch(plan, probs)
+    d = b.dev
+    net = sspcg.sspcg_mlp_create(1024)
+    lam0 = plan.empty(sspcg.ARRAY_VEC)
+    with pytest.raises(sspcg.SspcgError, match="unsupported"):
+        sspcg.sspcg_mlp_infer(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD, lam0)
+    with pytest.raises(sspcg.SspcgError, match="unsupported"):
+        sspcg.sspcg_mlp_fit_normalisation(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD)
+
+
 def _train(net, plan, b, lam_star, epochs, chunk, seed=0):
     """Minibatches of ``chunk`` consecutive problems in a seeded random order; mean loss per epoch."""
     d = b.dev
