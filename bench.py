@@ -362,11 +362,13 @@ def step_launches(probs, stats, lanes=True):
 def poly_comparison(args, torch, sspcg, stream, probs, w):
     """Polynomial preconditioners (Eq. polynomial_precon) on the benchmark workload: the whole pipeline step
     with Phi_d^-1 = sum_{j<=d} (I - Phi^-1 S)^j Phi^-1 for the symmetric stair at d = 0..3, and block-Jacobi
-    at d = 1 (the same preconditioner as the symmetric stair at d = 0, applied implicitly from D^-1 and S)."""
+    at d = 1 (the same preconditioner as the symmetric stair at d = 0, applied implicitly from D^-1 and S);
+    and the symmetric stair with single-reduction (Chronopoulos-Gear) PCG."""
     out = {}
-    for kind, deg in (("sym", 0), ("sym", 1), ("sym", 2), ("sym", 3), ("bj", 1)):
+    # (kind, degree, single-reduction PCG): the last entry is the textbook-equivalent single-reduction variant
+    for kind, deg, cg in (("sym", 0, 0), ("sym", 1, 0), ("sym", 2, 0), ("sym", 3, 0), ("bj", 1, 0), ("sym", 0, 1)):
         plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
-                                       sspcg.options(tol=w.tol, poly_degree=deg))
+                                       sspcg.options(tol=w.tol, poly_degree=deg, cg_variant=cg))
         b = sspcg.Batch(plan, probs)
         d = b.dev
 
@@ -386,9 +388,9 @@ def poly_comparison(args, torch, sspcg, stream, probs, w):
             torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         it = b.iters.cpu().numpy()
-        out[f"{kind}_d{deg}"] = {"solves_per_s": len(probs) / (ms / 1e3), "ms_per_step": ms,
-                                 "iters_mean": float(it.mean()),
-                                 "all_converged": bool((b.status.cpu().numpy() == 0).all())}
+        out[f"{kind}_d{deg}" + ("_single_reduction_cg" if cg else "")] = {
+            "solves_per_s": len(probs) / (ms / 1e3), "ms_per_step": ms, "iters_mean": float(it.mean()),
+            "all_converged": bool((b.status.cpu().numpy() == 0).all())}
         del b, plan
     return out
 

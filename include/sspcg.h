@@ -138,6 +138,12 @@ typedef struct {
                               positive definite), and then eig(Phi_d^-1 S) = 1 - (1 - theta)^(d+1) for the
                               eigenvalues theta of Phi^-1 S.  On the symmetric stair, degree d equals degree
                               2d+1 on the block-Jacobi splitting. */
+  int32_t cg_variant;      /* 0: textbook PCG (Saad Alg. 9.1).  1: single-reduction PCG (Chronopoulos and
+                              Gear 1989): the same iterates in exact arithmetic, s = S p kept by recurrence,
+                              and (r.u, S u.u, r.r) in one block sum per iteration (one barrier and one
+                              reduction tree fewer).  Run by the QP-form FP32 solves; requires
+                              SSPCG_REDUCE_DF and poly_degree = 0 (SSPCG_ERR_INVALID_ARG otherwise); the
+                              FP64 and block-form solves stay textbook.  iters counts x updates either way. */
 } sspcg_options;
 
 #define SSPCG_MAX_POLY_DEGREE 16

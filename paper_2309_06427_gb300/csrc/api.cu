@@ -83,23 +83,25 @@ int auto_block(int64_t rows) {
 
 // Staged block rows K and dynamic shared memory (bytes) of a PCG problem
 // under a schedule; false when even the vectors do not fit.
-bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int poly, int *K, int64_t *bytes) {
+// cg: the options ask for single-reduction PCG, which the QP-form FP32 launches run (two more vectors).
+bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int poly, int cg, int *K, int64_t *bytes) {
   const int64_t esz = f64 ? sizeof(double) : sizeof(float);
   const int64_t budget = smem_budget() / esz;
-  int k = pcg_max_resident(op, N, nx, nu, budget, poly > 0);
+  cg = (cg && op == kOpQp && !f64) ? 1 : 0;
+  int k = pcg_max_resident(op, N, nx, nu, budget, poly > 0, cg);
   if (k < 0) return false;
   // A problem that does not fit whole stages its first k block rows and streams the rest.  (Streaming
   // everything wins on a uniform batch of large problems, where it has the L2 bandwidth to itself, but
   // loses on the ragged batch, where the concurrent groups share it.)
   if (sched == SSPCG_SCHED_STREAM) k = 0;
   *K = k;
-  *bytes = pcg_layout(op, k, N, nx, nu, poly > 0).total * esz;
+  *bytes = pcg_layout(op, k, N, nx, nu, poly > 0, cg).total * esz;
   return true;
 }
 
 // Global-workspace slot (elements, a multiple of 4) of a problem whose vectors do not fit in shared memory.
-int64_t gvec_slot(int op, int N, int nx, int nu, int poly) {
-  return round_up(pcg_layout(op, 0, N, nx, nu, poly > 0).total, 4);
+int64_t gvec_slot(int op, int N, int nx, int nu, int poly, int cg) {
+  return round_up(pcg_layout(op, 0, N, nx, nu, poly > 0, cg && op == kOpQp).total, 4);
 }
 
 sspcg_status validate_opts(const sspcg_options *o) {
@@ -112,6 +114,8 @@ sspcg_status validate_opts(const sspcg_options *o) {
     return SSPCG_ERR_INVALID_ARG;
   if (o->precision < 0 || o->precision > 2) return SSPCG_ERR_INVALID_ARG;
   if (o->poly_degree < 0 || o->poly_degree > SSPCG_MAX_POLY_DEGREE) return SSPCG_ERR_INVALID_ARG;
+  if (o->cg_variant < 0 || o->cg_variant > 1) return SSPCG_ERR_INVALID_ARG;
+  if (o->cg_variant == 1 && (o->reduction != SSPCG_REDUCE_DF || o->poly_degree != 0)) return SSPCG_ERR_INVALID_ARG;
   return SSPCG_OK;
 }
 
@@ -126,8 +130,8 @@ namespace host {
 int sms() { return device_sms(); }
 int reduction_mode(int32_t r) { return red_mode(r); }
 int block_for_rows(int64_t rows) { return auto_block(rows); }
-bool fit(int op, int sched, int N, int nx, int nu, bool f64, int poly, int *K, int64_t *bytes) {
-  return pcg_fit(op, sched, N, nx, nu, f64, poly, K, bytes);
+bool fit(int op, int sched, int N, int nx, int nu, bool f64, int poly, int cg, int *K, int64_t *bytes) {
+  return pcg_fit(op, sched, N, nx, nu, f64, poly, cg, K, bytes);
 }
 sspcg_status check_options(const sspcg_options *o) { return validate_opts(o); }
 bool valid_shape(int N, int nx, int nu) { return shape_ok(N, nx, nu); }
@@ -301,12 +305,13 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
   for (int32_t i : members) {
     const ProbDesc &d = descs[i];
     int K = 0;
-    if (!pcg_fit(set.op, p->opts.schedule, d.N, d.nx, d.nu, set.f64, p->opts.poly_degree, &K, &bytes[i])) {
+    if (!pcg_fit(set.op, p->opts.schedule, d.N, d.nx, d.nu, set.f64, p->opts.poly_degree, p->opts.cg_variant, &K,
+                 &bytes[i])) {
       if (set.op != kOpQp) {  // global-vector kernels exist for the QP operator form only
         set.unsupported = true;
         continue;
       }
-      bytes[i] = gvec_slot(set.op, d.N, d.nx, d.nu, p->opts.poly_degree);  // slot elements
+      bytes[i] = gvec_slot(set.op, d.N, d.nx, d.nu, p->opts.poly_degree, set.f64 ? 0 : p->opts.cg_variant);
       buckets[kClasses * d.nx + 5].push_back(i);
       continue;
     }
@@ -365,6 +370,7 @@ PcgArgs make_args(const sspcg_options *o) {
   a.max_iter = o->max_iter;
   a.warm = o->warm_start;
   a.poly = o->poly_degree;
+  a.cg = o->cg_variant;
   a.lambda_f32 = 1;
   a.max_resident = o->schedule == SSPCG_SCHED_STREAM ? 0 : (1 << 30);
   return a;
@@ -532,7 +538,8 @@ static sspcg_status solve_single(int op, bool f64, int32_t N, int32_t nx, int32_
   if (op == kOpBlock && (!D || (N > 0 && !E))) return SSPCG_ERR_INVALID_ARG;
   int K = 0;
   int64_t bytes = 0;
-  if (!pcg_fit(op, opts->schedule, N, nx, nu, f64, opts->poly_degree, &K, &bytes)) return SSPCG_ERR_UNSUPPORTED;
+  if (!pcg_fit(op, opts->schedule, N, nx, nu, f64, opts->poly_degree, opts->cg_variant, &K, &bytes))
+    return SSPCG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   PcgArgs a = make_args(opts);
   a.ps = ProbSet{nullptr, single_desc(N, nx, nu), 1};

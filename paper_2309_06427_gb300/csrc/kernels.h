@@ -23,7 +23,7 @@ __host__ __device__ __forceinline__ int pad_ld(int x) { return x | 1; }
 // resident; K = 0: everything read from L2/HBM each iteration).  The same
 // function sizes launches on the host and carves on the device.
 struct PcgLayout {
-  int64_t p, r, w, x, e, v;         // vectors (e: the polynomial preconditioner's residual)
+  int64_t p, r, w, x, e, u, s, v;   // vectors (e: the polynomial's residual; u, s: single-reduction CG)
   int64_t iq, ir;                   // 1/q, 1/r (QP form)
   int64_t m0, m1, pd, pe;           // staged blocks
   int64_t total;
@@ -34,7 +34,7 @@ struct PcgLayout {
 // whole block-row segment with 128-bit loads.
 __host__ __device__ __forceinline__ int vec_stride(int x) { return (x + 3) & ~3; }
 
-__host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, int nu, int poly = 0) {
+__host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, int nu, int poly = 0, int cg = 0) {
   PcgLayout L{};
   const int64_t n = N + 1, NXP = vec_stride(nx), NUP = vec_stride(nu), RV = n * NXP;
   const int64_t Ks = K < N ? K : N;  // staged off-diagonal slots
@@ -46,6 +46,10 @@ __host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, in
   L.x = o; o += RV;
   L.e = o;
   if (poly) o += RV;
+  L.u = o;
+  if (cg) o += RV;
+  L.s = o;
+  if (cg) o += RV;
   L.v = o;
   if (op == kOpQp) o += RV + (int64_t)N * NUP;   // v_x then v_u
   L.iq = o;
@@ -67,13 +71,14 @@ __host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, in
 
 // Largest number of staged block rows whose layout fits in ``elems``; -1 when
 // not even the vectors fit.
-__host__ __device__ inline int pcg_max_resident(int op, int N, int nx, int nu, int64_t elems, int poly = 0) {
-  if (pcg_layout(op, N + 1, N, nx, nu, poly).total <= elems) return N + 1;
-  if (pcg_layout(op, 0, N, nx, nu, poly).total > elems) return -1;
+__host__ __device__ inline int pcg_max_resident(int op, int N, int nx, int nu, int64_t elems, int poly = 0,
+                                                int cg = 0) {
+  if (pcg_layout(op, N + 1, N, nx, nu, poly, cg).total <= elems) return N + 1;
+  if (pcg_layout(op, 0, N, nx, nu, poly, cg).total > elems) return -1;
   int lo = 0, hi = N;  // invariant: layout(lo) fits, layout(hi + 1) does not
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
-    if (pcg_layout(op, mid, N, nx, nu, poly).total <= elems) lo = mid; else hi = mid - 1;
+    if (pcg_layout(op, mid, N, nx, nu, poly, cg).total <= elems) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -97,6 +102,7 @@ struct PcgArgs {
   int32_t max_iter;      // <= 0: 10 (N+1) nx
   int32_t warm;          // 0, 1, 2 (see sspcg_options)
   int32_t poly;          // degree d of the polynomial preconditioner sum_{j<=d} (I - Phi^-1 S)^j Phi^-1
+  int32_t cg;            // 1: single-reduction (Chronopoulos-Gear) PCG (QP form, FP32, double-float sums)
   int64_t smem_elems;    // dynamic shared memory of the launch, in elements of the working precision
   int32_t max_resident;  // cap on staged block rows (a schedule override); large = no cap
   void *gscratch;        // vectors in global memory: CTA b uses gscratch + b * gstride elements

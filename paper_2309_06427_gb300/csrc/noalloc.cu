@@ -16,7 +16,7 @@ namespace host {  // defined in api.cu
 int sms();
 int reduction_mode(int32_t r);
 int block_for_rows(int64_t rows);
-bool fit(int op, int sched, int N, int nx, int nu, bool f64, int poly, int *K, int64_t *bytes);
+bool fit(int op, int sched, int N, int nx, int nu, bool f64, int poly, int cg, int *K, int64_t *bytes);
 sspcg_status check_options(const sspcg_options *o);
 bool valid_shape(int N, int nx, int nu);
 sspcg_status cuda_error(cudaError_t e);
@@ -97,7 +97,7 @@ extern "C" sspcg_status sspcg_solve_qp_batched_noalloc(int32_t nprob, const int3
     d.oA = off[SSPCG_ARRAY_A]; d.oB = off[SSPCG_ARRAY_B]; d.oq = off[SSPCG_ARRAY_QD]; d.orr = off[SSPCG_ARRAY_RD];
     d.odiag = off[SSPCG_ARRAY_DIAG]; d.ooff = off[SSPCG_ARRAY_OFF]; d.ovec = off[SSPCG_ARRAY_VEC];
     int K = 0;
-    if (!host::fit(kOpQp, opts->schedule, d.N, d.nx, d.nu, false, opts->poly_degree, &K, &bytes[i]))
+    if (!host::fit(kOpQp, opts->schedule, d.N, d.nx, d.nu, false, opts->poly_degree, opts->cg_variant, &K, &bytes[i]))
       return SSPCG_ERR_UNSUPPORTED;
     by_nx[d.nx].push_back(i);
   }
@@ -155,6 +155,7 @@ extern "C" sspcg_status sspcg_solve_qp_batched_noalloc(int32_t nprob, const int3
   a.max_iter = opts->max_iter;
   a.warm = opts->warm_start;
   a.poly = opts->poly_degree;
+  a.cg = opts->cg_variant;
   a.lambda_f32 = 1;
   a.max_resident = opts->schedule == SSPCG_SCHED_STREAM ? 0 : (1 << 30);
   for (const Group &g : groups) {

@@ -170,7 +170,7 @@ struct Views {
   int ld, ldb;                                    // staged row strides
 };
 
-template <int NX, int OP, int RED, typename Real>
+template <int NX, int OP, int RED, typename Real, bool CG = false>
 __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typename Red<RED, Real>::T *slots) {
   using R = Red<RED, Real>;
   using AccT = typename R::T;
@@ -179,12 +179,13 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   const int N = d.N, n = N + 1, nu = d.nu, R_ = n * NX, NUP = vec_stride(nu);
   const int tid = threadIdx.x, T = blockDim.x;
   const int poly = a.poly;
-  int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems, poly > 0);  // the host sized smem so that K >= 0
+  int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems, poly > 0, CG);  // the host sized smem so that K >= 0
   if (K > a.max_resident) K = a.max_resident;
   if (K < 0) K = 0;
   const int Ks = K < N ? K : N;
-  const PcgLayout L = pcg_layout(OP, K, N, NX, nu, poly > 0);
+  const PcgLayout L = pcg_layout(OP, K, N, NX, nu, poly > 0, CG);
   Real *sp = sm + L.p, *sr = sm + L.r, *sw = sm + L.w, *sx = sm + L.x, *sv = sm + L.v, *se = sm + L.e;
+  Real *su = sm + L.u, *ss = sm + L.s;
   Real *svu = sv + n * NXP;  // v_u block rows, stride NUP
   const float *gam = a.gamma + d.ovec;
   // lambda (global): read once for a warm start, written once at the end
@@ -393,6 +394,94 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     }
   }
   __syncthreads();
+  if constexpr (CG) {
+    // Single-reduction PCG (Chronopoulos & Gear 1989): the same iterates as the textbook algorithm, with
+    // s = S p kept by recurrence, so that r.u, S u.u and r.r come from one block sum per iteration:
+    //   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, barrier,
+    //   u = Phi^-1 r, barrier, w = S u (QP form: phase 1, barrier, phase 2) with the three sums,
+    //   beta = (r.u)new / (r.u), alpha = (r.u)new / ((S u.u) - beta (r.u)new / alpha)
+    // since p.S p = S u.u - beta (r.u)new / alpha for the new p.  iters counts x updates, as textbook.
+    Real ru = Real(0), del = Real(0), rr = Real(0);  // r.u, S u.u, r.r
+    auto u_w_sums = [&]() {
+      for (int row = tid; row < R_; row += T) {
+        int k, i;
+        const int si = vid(row, k, i);  // sets k, i: its own statement, before they are read
+        su[si] = apply_P_row(sr, k, i);
+      }
+      __syncthreads();
+      apply_S_phase1(su);
+      AccT s3[3] = {R::zero(), R::zero(), R::zero()};
+      for (int row = tid; row < R_; row += T) {
+        int k, i;
+        const int si = vid(row, k, i);
+        const Real w = apply_S_row(su, k, i);
+        const Real u = su[si], r = sr[si];
+        sw[si] = w;
+        s3[0] = R::fma(s3[0], r, u);
+        s3[1] = R::fma(s3[1], w, u);
+        s3[2] = R::fma(s3[2], r, r);
+      }
+      block_sum<R, 3>(s3, slots);
+      ru = R::get(s3[0]);
+      del = R::get(s3[1]);
+      rr = R::get(s3[2]);
+    };
+    for (int pass = 0; pass < 2; ++pass) {
+      u_w_sums();
+      if (pass == 0 && warm && a.warm == 2 && !(rr < gg)) {  // warm start no better than zero: restart
+        for (int row = tid; row < R_; row += T) {
+          int k, i;
+          const int si = vid(row, k, i);
+          sr[si] = (Real)gam[row];
+          sx[si] = Real(0);
+        }
+        warm = false;
+        __syncthreads();
+        continue;
+      }
+      break;
+    }
+    int it = 0, code = kOk;
+    Real alpha = ru / del, beta = Real(0);
+    if (!(del > Real(0)) || !isfinite(del)) code = isfinite(del) ? kBreakdown : kNonFinite;
+    while (code == kOk) {
+      if (!(rr > thresh)) {
+        if (!isfinite(rr)) code = kNonFinite;
+        break;
+      }
+      if (it >= max_iter) { code = kMaxIter; break; }
+      for (int row = tid; row < R_; row += T) {
+        int k, i;
+        const int si = vid(row, k, i);
+        const Real pn = it == 0 ? su[si] : rfma(beta, sp[si], su[si]);
+        const Real sn = it == 0 ? sw[si] : rfma(beta, ss[si], sw[si]);
+        sp[si] = pn;
+        ss[si] = sn;
+        sx[si] = rfma(alpha, pn, sx[si]);
+        sr[si] = rfma(-alpha, sn, sr[si]);
+      }
+      __syncthreads();
+      const Real ru_old = ru;
+      u_w_sums();
+      ++it;
+      beta = ru / ru_old;
+      const Real den = del - beta * ru / alpha;
+      if (!(rr > thresh)) continue;  // converged: the next step is not taken
+      if (!(den > Real(0)) || !isfinite(den)) { code = isfinite(den) ? kBreakdown : kNonFinite; break; }
+      alpha = ru / den;
+    }
+    for (int row = tid; row < R_; row += T) {
+      int k, i;
+      lam_store(row, sx[vid(row, k, i)]);
+    }
+    if (tid == 0) {
+      a.iters[p] = it;
+      a.relres[p] = sqrt((double)rr / (double)gg);
+      a.status[p] = code;
+    }
+    __syncthreads();
+    return;
+  }
   Real rz, rr;
   for (int pass = 0; pass < 2; ++pass) {
     precondition(rz, rr);
@@ -475,7 +564,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
 // atomic counter when one is given (largest problems first), else by stride.
 // GV: vectors in this CTA's slot of a global workspace (problems whose vectors do not fit in shared
 // memory).  A compile-time choice, so that the other launches address their vectors as shared memory.
-template <int NX, int OP, int RED, typename Real, bool GV>
+template <int NX, int OP, int RED, typename Real, bool GV, bool CG = false>
 __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
   extern __shared__ float4 smem4[];
   Real *sm;
@@ -498,13 +587,13 @@ __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
     if (w >= a.nwork) break;
     const ProbDesc d = a.ps.get(a.work ? a.work[w] : w);
     if (a.status[d.id] != kOk) continue;  // preconditioner failed for this problem
-    pcg_solve<NX, OP, RED, Real>(a, d, sm, slots);
+    pcg_solve<NX, OP, RED, Real, CG>(a, d, sm, slots);
   }
 }
 
-template <int NX, int OP, int RED, typename Real, bool GV>
+template <int NX, int OP, int RED, typename Real, bool GV, bool CG = false>
 cudaError_t launch_variant(const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
-  auto k = pcg_kernel<NX, OP, RED, Real, GV>;
+  auto k = pcg_kernel<NX, OP, RED, Real, GV, CG>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_max_smem_bytes());
@@ -519,10 +608,16 @@ cudaError_t launch_variant(const PcgArgs &a, int grid, int block, size_t smem, c
 
 // All variants of one nx: FP32 with three reduction modes for both operator
 // forms, and the FP64 path (QP form, FP64 reductions); vectors in a global
-// workspace for the QP form only.
+// workspace for the QP form only; single-reduction PCG for the QP form with
+// FP32 arithmetic and double-float sums.
 template <int NX>
 cudaError_t launch_pcg_for_nx(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
                               cudaStream_t st) {
+  if (a.cg && op == kOpQp && !f64) {  // single-reduction PCG (the FP64 and block-form launches stay textbook)
+    if (red != kRedDf) return cudaErrorInvalidValue;
+    if (a.gscratch) return launch_variant<NX, kOpQp, kRedDf, float, true, true>(a, grid, block, smem, st);
+    return launch_variant<NX, kOpQp, kRedDf, float, false, true>(a, grid, block, smem, st);
+  }
   if (a.gscratch) {
     if (op != kOpQp) return cudaErrorInvalidValue;
     if (f64) return launch_variant<NX, kOpQp, kRedF64, double, true>(a, grid, block, smem, st);

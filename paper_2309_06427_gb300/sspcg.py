@@ -36,17 +36,17 @@ class SspcgError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("reduction", ctypes.c_int32), ("schedule", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("poly_degree", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("poly_degree", ctypes.c_int32), ("cg_variant", ctypes.c_int32)]
 
 
 MAX_POLY_DEGREE = 16
 
 
 def options(tol=1e-6, max_iter=0, warm_start=0, reduction="df", schedule="auto", block_threads=0,
-            precision="auto", poly_degree=0) -> Options:
+            precision="auto", poly_degree=0, cg_variant=0) -> Options:
     pick = lambda table, v: table[v] if isinstance(v, str) else int(v)
     return Options(float(tol), int(max_iter), int(warm_start), pick(REDUCE, reduction), pick(SCHED, schedule),
-                   int(block_threads), pick(PRECISION, precision), int(poly_degree))
+                   int(block_threads), pick(PRECISION, precision), int(poly_degree), int(cg_variant))
 
 
 _lib = None
