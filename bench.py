@@ -36,14 +36,15 @@ SMEM_BYTES_PER_CLK_PER_SM = 128  # shared-memory bandwidth of one SM (32 banks x
 MLP_FLOP_PER_ROW = 2 * (1344 * 256 + 256 * 256 + 256 * 32)  # warm-start network forward, one knot row
 def pcg_traffic():
     """DRAM bytes of one PCG-only solve of the benchmark batch, from the committed ncu launch-list summary,
-    if the kernel and planner sources are unchanged since it was captured; else None."""
+    if the kernel source (pcg.cuh and its layout and arguments in kernels.h) is unchanged since it was
+    captured; else None."""
     import hashlib
     try:
         text = open(os.path.join(ROOT, "profiles", "launches_ragged4096_pipeline.md")).read()
         vals = dict(line.split(":", 1) for line in text.splitlines()
                     if line.startswith(("pcg_traffic_bytes_per_solve:", "source_sha256_16:")))
         h = hashlib.sha256()
-        for f in ("pcg.cuh", "api.cu"):
+        for f in ("pcg.cuh", "kernels.h"):
             with open(os.path.join(ROOT, "paper_2309_06427_gb300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
         if h.hexdigest()[:16] != vals["source_sha256_16"].strip():
