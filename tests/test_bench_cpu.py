@@ -1,0 +1,51 @@
+"""Host helpers of bench.py: the kernel-launch count of a step, the guard that ties the recorded PCG
+traffic to the kernel source, the per-iteration algorithmic bytes and the whole-job throughput."""
+import os
+import shutil
+
+import pytest
+
+import bench
+from paper_2309_06427_gb300 import problems as P
+
+
+def test_step_launches_count_per_nx_lane():
+    """Ragged batch: 4 nx lanes x (Schur, D^-1, off-diagonal) + FP64 lane (Schur, one D^-1 per tiny nx,
+    off-diagonal) + one launch per PCG group: 12 + 3 + 15 = 30, as the ncu launch list of one step shows."""
+    probs = P.make_workload(P.RAGGED_BATCH_4096, count=400)
+    nxs = {p.nx for p in probs}
+    tiny_nx = {p.nx for p in probs if (p.N + 1) * p.nx <= 192}
+    assert nxs == {4, 12, 14, 21} and tiny_nx == {4}
+    stats = {"pipeline_f64": 1, "pipeline_launches": 15}
+    assert bench.step_launches(probs, stats) == 30
+    # the two-half pipeline builds every problem in one Schur and one off-diagonal launch
+    assert bench.step_launches(probs, stats, lanes=False) == 2 + 4 + 3 + 15
+    # no FP64 subset: no FP64 build launches
+    assert bench.step_launches(probs, {"pipeline_f64": 0, "pipeline_launches": 15}) == 12 + 15
+
+
+def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    assert isinstance(bench.pcg_traffic(), int)
+    # a copy of the tree whose kernel source differs: the recorded figure no longer applies
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    (root / "paper_2309_06427_gb300" / "csrc").mkdir(parents=True)
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "launches_ragged4096_pipeline.md"), root / "profiles")
+    for f in ("pcg.cuh", "kernels.h"):
+        shutil.copy(os.path.join(bench.ROOT, "paper_2309_06427_gb300", "csrc", f),
+                    root / "paper_2309_06427_gb300" / "csrc" / f)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.pcg_traffic() == int(open(os.path.join(root, "profiles", "launches_ragged4096_pipeline.md"))
+                                      .read().split("pcg_traffic_bytes_per_solve:")[1].split()[0])
+    with open(root / "paper_2309_06427_gb300" / "csrc" / "pcg.cuh", "a") as f:
+        f.write("\n// changed\n")
+    assert bench.pcg_traffic() is None
+
+
+def test_algorithmic_bytes_and_throughput():
+    p = P.custom_problems([(3, 2, 1)], config=88)[0]
+    # A 3*4, B 3*2, diag Q 4*2, diag R 3, PD 4*4, PE 3*4, vectors 10 * 4*2 floats
+    assert bench.algorithmic_bytes_per_iteration(p) == 4 * (12 + 6 + 8 + 3 + 16 + 12 + 80)
+    # 2 ranks x 100 problems x 10 steps in 20 ms (slowest rank)
+    assert bench.job_throughput(2, 100, 10, 20.0) == pytest.approx(100_000.0)
+    assert bench.rank_start(3, 4096) == 3 * 4096
