@@ -1,5 +1,6 @@
 // C ABI of sspcg: argument validation, batch plans, schedules and launches.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
@@ -160,6 +161,7 @@ struct PcgGroup {
   int32_t *d_work = nullptr;  // slice of the plan's work array
   int32_t nwork = 0;
   int counter_index = 0;
+  double work = 0.0;  // estimated PCG work: sum over members of (N+1)^1.5 nx (3 nx + nu)
 };
 
 // A set of problems solved by one group of PCG launches (one per nx and schedule).
@@ -337,6 +339,8 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
         const ProbDesc &d = descs[i];
         maxrows = std::max<int64_t>(maxrows, (int64_t)(d.N + 1) * d.nx);
         maxsmem = std::max<int64_t>(maxsmem, bytes[i]);
+        // bytes per iteration times iterations, which grow about as sqrt(N + 1)
+        g.work += std::pow((double)(d.N + 1), 1.5) * d.nx * (3.0 * d.nx + d.nu);
       }
       g.block = p->opts.block_threads > 0 ? p->opts.block_threads : auto_block(maxrows);
       const int by_thr = std::max(1, 2048 / g.block);
@@ -405,6 +409,9 @@ sspcg_status launch_sets(sspcg_plan *p, std::initializer_list<SetLaunch> list, c
   for (const SetLaunch &sl : list)
     for (const PcgGroup &g : sl.set->groups) all.push_back({&g, &sl.args, sl.set});
   if (all.empty()) return SSPCG_OK;
+  // heaviest group first: the persistent CTAs of the longest launch take their SMs first and the lighter
+  // launches fill in around them, which shortens the tail
+  std::stable_sort(all.begin(), all.end(), [](const Item &x, const Item &y) { return x.g->work > y.g->work; });
   SSPCG_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int32_t) * p->ngroups_total, st));
   const size_t ng = all.size();
   if (ng > 1) {
@@ -1042,6 +1049,8 @@ static sspcg_status pipeline_lanes(sspcg_plan *p, sspcg_precond kind, const floa
     }
     return SSPCG_OK;
   };
+  // lanes in increasing nx: launching the heaviest lane first (as launch_sets does with its groups) made the
+  // ragged batch's step 1.8 % slower, its build holding SMs that the lighter lanes' solves would use
   for (size_t i = 0; i < p->nxg_all.size(); ++i) {
     const NxGroup &g = p->nxg_all[i];
     cudaStream_t L = p->lanes[i];
