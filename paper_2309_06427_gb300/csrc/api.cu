@@ -219,9 +219,6 @@ struct sspcg_plan {
   GroupSet sets[kNumSets];
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;
-  // pipeline lanes: one stream per nx group (and one for the FP64 subset)
-  std::vector<cudaStream_t> lanes;
-  std::vector<cudaEvent_t> lane_ev;
   // phase timing (opt-in)
   bool timing = false;
   cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
@@ -286,8 +283,6 @@ void plan_free(sspcg_plan *p) {
   if (p->d2h) cudaStreamDestroy(p->d2h);
   for (auto s : p->side) cudaStreamDestroy(s);
   for (auto e : p->ev) cudaEventDestroy(e);
-  for (auto s : p->lanes) cudaStreamDestroy(s);
-  for (auto e : p->lane_ev) cudaEventDestroy(e);
   for (auto e : p->tev)
     if (e) cudaEventDestroy(e);
   delete p;
@@ -716,13 +711,6 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     p->side.resize(nside);
     for (auto &s2 : p->side)
       if ((e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking)) != cudaSuccess) return fail(cuda_fail(e));
-    const size_t nlanes = p->nxg_all.size() + (p->ntiny > 0 ? 1 : 0);
-    p->lanes.resize(nlanes);
-    for (auto &s2 : p->lanes)
-      if ((e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking)) != cudaSuccess) return fail(cuda_fail(e));
-    p->lane_ev.resize(3 * nlanes + p->sets[kSetQpMain].groups.size() + p->sets[kSetTiny].groups.size() + 1);
-    for (auto &ev : p->lane_ev)
-      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(cuda_fail(e));
   }
   *plan = p;
   return SSPCG_OK;
@@ -996,106 +984,6 @@ static sspcg_status pipeline_solve(sspcg_plan *plan, const float *A, const float
   return s;
 }
 
-// The pipeline in lanes: one stream per nx group builds that group's FP32 blocks and preconditioner and
-// then runs its PCG groups (FP32 set); one more lane builds the FP64 blocks of the FP64 subset and solves
-// it.  A lane's build overlaps the other lanes' solves; every lane joins back into ``st``.
-static sspcg_status pipeline_lanes(sspcg_plan *p, sspcg_precond kind, const float *A, const float *B,
-                                   const float *qd, const float *rd, const float *gamma, float *D, float *E, float *PD,
-                                   float *PE, float *lambda, int32_t *iters, double *relres, int32_t *status, int warm,
-                                   cudaStream_t st) {
-  const int sms = device_sms();
-  SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * p->nprob, st));
-  SSPCG_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int32_t) * std::max(1, p->ngroups_total), st));
-  time_mark(p, 0, st);
-  size_t evi = 0, sidei = 0;
-  cudaEvent_t fork = p->lane_ev[evi++];
-  SSPCG_CUDA(cudaEventRecord(fork, st));
-  PcgArgs a32 = batched_args(p, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
-  a32.warm = warm;
-  PcgArgs a64 = a32;
-  a64.ps = tiny_set(p);
-  a64.PD = p->PD64;
-  a64.PE = p->PE64;
-  std::vector<cudaEvent_t> built, done;
-  // PCG groups of ``set`` with this nx (every group when nx == 0): the first on the lane, the others on
-  // side streams forked from it after the lane's build
-  auto solve_groups = [&](const GroupSet &set, const PcgArgs &base, int nx, cudaStream_t lane) -> sspcg_status {
-    bool first = true;
-    cudaEvent_t ready = nullptr;
-    for (const PcgGroup &g : set.groups) {
-      if (nx != 0 && g.nx != nx) continue;
-      cudaStream_t s = lane;
-      if (!first) {
-        if (!ready) {
-          ready = p->lane_ev[evi++];
-          SSPCG_CUDA(cudaEventRecord(ready, lane));
-        }
-        s = p->side[sidei++];
-        SSPCG_CUDA(cudaStreamWaitEvent(s, ready, 0));
-      }
-      PcgArgs a = base;
-      a.work = g.d_work;
-      a.nwork = g.nwork;
-      a.counter = p->d_counters + g.counter_index;
-      set_gvec(a, p, set, g);
-      const int red = g.f64 ? kRedF64 : red_mode(p->opts.reduction);
-      SSPCG_CUDA(launch_pcg(g.nx, set.op, red, g.f64, a, g.grid, g.block, g.smem, s));
-      if (!first) {
-        cudaEvent_t e = p->lane_ev[evi++];
-        SSPCG_CUDA(cudaEventRecord(e, s));
-        done.push_back(e);
-      }
-      first = false;
-    }
-    return SSPCG_OK;
-  };
-  // lanes in increasing nx (launching the heaviest lane first, as launch_sets orders its groups, measured
-  // 1.8 % slower on the ragged batch)
-  for (size_t i = 0; i < p->nxg_all.size(); ++i) {
-    const NxGroup &g = p->nxg_all[i];
-    cudaStream_t L = p->lanes[i];
-    const ProbSet ps{g.d_desc, ProbDesc{}, g.nprob};
-    SSPCG_CUDA(cudaStreamWaitEvent(L, fork, 0));
-    SSPCG_CUDA(launch_schur_build<float>(ps, g.d_refs, g.knots, A, B, qd, rd, D, E, L, sms, g.mx));
-    SSPCG_CUDA(launch_precond_inv<float>(ps, g.d_refs, g.knots, g.nx, (int)kind, D, PD, status, L));
-    SSPCG_CUDA(launch_precond_off<float>(ps, g.d_orefs, g.offs, (int)kind, E, PD, PE, L, sms,
-                                         p->sizes[SSPCG_ARRAY_OFF], g.mx));
-    cudaEvent_t b = p->lane_ev[evi++];
-    SSPCG_CUDA(cudaEventRecord(b, L));
-    built.push_back(b);
-    sspcg_status s = solve_groups(p->sets[kSetQpMain], a32, g.nx, L);
-    if (s != SSPCG_OK) return s;
-    cudaEvent_t e = p->lane_ev[evi++];
-    SSPCG_CUDA(cudaEventRecord(e, L));
-    done.push_back(e);
-  }
-  if (p->ntiny > 0) {
-    cudaStream_t T = p->lanes[p->nxg_all.size()];
-    SSPCG_CUDA(cudaStreamWaitEvent(T, fork, 0));
-    SSPCG_CUDA(launch_schur_build<double>(tiny_set(p), p->d_tkref, p->tknots, A, B, qd, rd, p->D64, p->E64, T, sms,
-                                          p->mx_tiny));
-    for (const NxGroup &g : p->nxg_tiny)
-      SSPCG_CUDA(launch_precond_inv<double>(ProbSet{g.d_desc, ProbDesc{}, g.nprob}, g.d_refs, g.knots, g.nx,
-                                            (int)kind, p->D64, p->PD64, status, T));
-    SSPCG_CUDA(launch_precond_off<double>(tiny_set(p), p->d_toref, p->toff, (int)kind, p->E64, p->PD64, p->PE64, T,
-                                          sms, p->t_offe, p->mx_tiny));
-    cudaEvent_t b = p->lane_ev[evi++];
-    SSPCG_CUDA(cudaEventRecord(b, T));
-    built.push_back(b);
-    sspcg_status s = solve_groups(p->sets[kSetTiny], a64, 0, T);
-    if (s != SSPCG_OK) return s;
-    cudaEvent_t e = p->lane_ev[evi++];
-    SSPCG_CUDA(cudaEventRecord(e, T));
-    done.push_back(e);
-  }
-  for (cudaEvent_t b : built) SSPCG_CUDA(cudaStreamWaitEvent(st, b, 0));
-  p->build_timed = true;
-  time_mark(p, 1, st);  // the last lane's build is done (solves of other lanes may be running)
-  for (cudaEvent_t e : done) SSPCG_CUDA(cudaStreamWaitEvent(st, e, 0));
-  time_mark(p, 2, st);
-  return SSPCG_OK;
-}
-
 sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
                                     const float *qd, const float *rd, const float *gamma, float *D, float *E,
                                     float *PD, float *PE, float *lambda, int32_t *iters, double *relres,
@@ -1107,8 +995,10 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
   if (s != SSPCG_OK) return s;
   if (!D || (plan->total_off > 0 && !E)) return SSPCG_ERR_INVALID_ARG;
   if (!aligned16(qd) || !aligned16(D)) return SSPCG_ERR_INVALID_ARG;
-  return pipeline_lanes(plan, kind, A, B, qd, rd, gamma, D, E, PD, PE, lambda, iters, relres, status,
-                        plan->opts.warm_start, (cudaStream_t)stream);
+  s = pipeline_build(plan, kind, A, B, qd, rd, D, E, PD, PE, status, stream);
+  if (s != SSPCG_OK) return s;
+  return pipeline_solve(plan, A, B, qd, rd, gamma, PD, PE, lambda, iters, relres, status, plan->opts.warm_start,
+                        stream);
 }
 
 sspcg_status sspcg_plan_capture_pipeline(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
