@@ -334,8 +334,7 @@ def warm_start_comparison(args, torch, sspcg, stream, rank):
         infer[engine] = {"ms": ms, "tflops": rows * MLP_FLOP_PER_ROW / (ms / 1e3) / 1e12}
     sspcg.sspcg_mlp_set_engine(net, "tcgen05")
     stats = sspcg.plan_stats(plan)
-    # plain steps in lanes; warm steps: the two-half pipeline plus, per chunk of MLP_MAX_ROWS rows, features,
-    # three products and the scatter
+    # warm steps add, per chunk of MLP_MAX_ROWS rows, features, three products and the scatter
     chunks = -(-sum(p.n for p in probs) // MLP_MAX_ROWS)
     return {"workload": w.name, "train_problems": args.train_problems, "train_solves": ntrain,
             "train_epochs": args.train_epochs,
@@ -343,21 +342,18 @@ def warm_start_comparison(args, torch, sspcg, stream, rank):
             "plain": out["plain"], "warm": out["warm"],
             "inference": {"rows": rows, "flop_per_row": MLP_FLOP_PER_ROW, **infer},
             "speedup": out["warm"]["solves_per_s"] / out["plain"]["solves_per_s"],
-            "gpu_launches": args.steps * (step_launches(probs, stats) + step_launches(probs, stats, lanes=False) +
-                                          5 * chunks)}
+            "gpu_launches": args.steps * (2 * step_launches(probs, stats) + 5 * chunks)}
 
 
-def step_launches(probs, stats, lanes=True):
-    """Kernel launches of one pipeline step.  In lanes (sspcg_pipeline_batched) every nx group builds its own
-    Schur blocks, D_k^-1 and off-diagonal blocks (3 launches per nx); the two-half pipeline (the warm-start
-    path) builds every problem in one Schur launch, one D_k^-1 launch per nx and one off-diagonal launch.  The
-    FP64 subset (at most 192 unknowns) adds its Schur launch, one D_k^-1 launch per nx and its off-diagonal
-    launch; then one PCG launch per group."""
+def step_launches(probs, stats):
+    """Kernel launches of one pipeline step: every problem's Schur blocks in one launch, the D_k^-1 blocks in
+    one launch per nx, the off-diagonal preconditioner blocks in one launch; the FP64 subset (at most 192
+    unknowns) adds its Schur launch, one D_k^-1 launch per nx and its off-diagonal launch; then one PCG
+    launch per group."""
     nxs = {p.nx for p in probs}
     tiny_nx = {p.nx for p in probs if (p.N + 1) * p.nx <= 192}
-    fp32 = 3 * len(nxs) if lanes else 2 + len(nxs)
     fp64 = 2 + len(tiny_nx) if stats["pipeline_f64"] else 0
-    return fp32 + fp64 + stats["pipeline_launches"]
+    return 2 + len(nxs) + fp64 + stats["pipeline_launches"]
 
 
 def poly_comparison(args, torch, sspcg, stream, probs, w):

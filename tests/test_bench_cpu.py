@@ -9,19 +9,16 @@ import bench
 from paper_2309_06427_gb300 import problems as P
 
 
-def test_step_launches_count_per_nx_lane():
-    """Ragged batch: 4 nx lanes x (Schur, D^-1, off-diagonal) + FP64 lane (Schur, one D^-1 per tiny nx,
-    off-diagonal) + one launch per PCG group: 12 + 3 + 15 = 30, as the ncu launch list of one step shows."""
+def test_step_launches_count():
+    """Ragged batch: Schur + one D^-1 launch per nx (4) + off-diagonal, the FP64 subset's Schur + one D^-1
+    per tiny nx (1) + off-diagonal, and one launch per PCG group (15): 6 + 3 + 15 = 24."""
     probs = P.make_workload(P.RAGGED_BATCH_4096, count=400)
     nxs = {p.nx for p in probs}
     tiny_nx = {p.nx for p in probs if (p.N + 1) * p.nx <= 192}
     assert nxs == {4, 12, 14, 21} and tiny_nx == {4}
-    stats = {"pipeline_f64": 1, "pipeline_launches": 15}
-    assert bench.step_launches(probs, stats) == 30
-    # the two-half pipeline builds every problem in one Schur and one off-diagonal launch
-    assert bench.step_launches(probs, stats, lanes=False) == 2 + 4 + 3 + 15
+    assert bench.step_launches(probs, {"pipeline_f64": 1, "pipeline_launches": 15}) == 24
     # no FP64 subset: no FP64 build launches
-    assert bench.step_launches(probs, {"pipeline_f64": 0, "pipeline_launches": 15}) == 12 + 15
+    assert bench.step_launches(probs, {"pipeline_f64": 0, "pipeline_launches": 15}) == 6 + 15
 
 
 def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
