@@ -341,6 +341,11 @@ sspcg_status sspcg_residual_qp_batched(sspcg_plan *plan, const float *A, const f
  * preconditioner, PCG with the factored S.  D, E, PD, PE are caller work
  * buffers of the packed sizes.  A problem whose preconditioner fails keeps
  * status SSPCG_SOLVE_NOT_SPD and is not iterated.
+ * Schedule: every problem's blocks are built first (FP32, and FP64 for the
+ * FP64 subset the plan's precision option selects); then all PCG launch
+ * groups run concurrently on plan-owned streams forked from ``stream``,
+ * the group with the most estimated work first, and join back into it.
+ * Capturable as a CUDA graph (sspcg_plan_capture_pipeline).
  */
 sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
                                     const float *qd, const float *rd, const float *gamma, float *D, float *E,
