@@ -91,3 +91,27 @@ def test_product_code_never_imports_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
                 assert "sspcg_oracle" not in txt and "liboracle" not in txt, f
+
+
+def _declared_arity():
+    """Parameter count of every function the header declares (comments removed, depth-0 commas)."""
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"^\s*(?:sspcg_status|const char \*)\s*(sspcg_\w+)\s*\(([^;]*?)\)\s*;", txt, re.M | re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header(L):
+    """Every ctypes signature the binding sets has the header's parameter count (a wrong count passes
+    garbage for the trailing arguments)."""
+    arity = _declared_arity()
+    assert len(arity) >= 40
+    checked = 0
+    for name, n in arity.items():
+        f = getattr(L, name)
+        if f.argtypes is not None:
+            assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+            checked += 1
+    assert checked >= 40
