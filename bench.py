@@ -630,9 +630,8 @@ def main():
     ok = bool((status == 0).all() and (relres <= w.tol).all())
     value = job_throughput(world, nprob, args.steps, total_ms)
 
-    # The pipeline overlaps one nx lane's build with the other lanes' solves, so the phases are timed
-    # apart: the PCG launches alone (FP32, every problem, all groups concurrently) on the blocks the
-    # pipeline built, and the two build calls alone.
+    # The phases timed apart: the PCG launches alone (FP32, every problem, all groups concurrently) on the
+    # blocks the pipeline built, and the two build calls alone.
     it_d = torch.zeros_like(b.iters); rr_d = torch.zeros_like(b.relres); st_d = torch.zeros_like(b.status)
     lam_d = torch.zeros_like(b.lam)
 
