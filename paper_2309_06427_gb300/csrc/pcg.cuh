@@ -18,6 +18,9 @@
 //      e = S-residual r - S z, barrier, z += Phi^-1 e; the sums after the last)
 //   beta = (r.z)new / (r.z)old, p = z + beta p, barrier
 // Stop before an iteration once r.r <= tol^2 gamma.gamma.
+// The CG template flag selects the single-reduction form of the same
+// iteration (Chronopoulos & Gear): s = S p by recurrence, one block sum of
+// (r.u, S u.u, r.r) per iteration; see the CG section of pcg_solve.
 //
 // The first K block rows of the operator and preconditioner blocks are
 // staged in shared memory (odd row strides); the rest are read from global
