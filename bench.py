@@ -34,20 +34,28 @@ WORKLOAD = P.RAGGED_BATCH_4096
 PRECOND = "sym"
 SMEM_BYTES_PER_CLK_PER_SM = 128  # shared-memory bandwidth of one SM (32 banks x 4 B per clock)
 MLP_FLOP_PER_ROW = 2 * (1344 * 256 + 256 * 256 + 256 * 32)  # warm-start network forward, one knot row
+def kernel_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the PCG kernel source (pcg.cuh, and its layout and arguments in
+    kernels.h) with comments and blank space removed, so that only code changes alter it."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in ("pcg.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2309_06427_gb300", "csrc", f)) as fh:
+            src = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
+    return h.hexdigest()[:16]
+
+
 def pcg_traffic():
     """DRAM bytes of one PCG-only solve of the benchmark batch, from the committed ncu launch-list summary,
-    if the kernel source (pcg.cuh and its layout and arguments in kernels.h) is unchanged since it was
-    captured; else None."""
-    import hashlib
+    if the kernel source is unchanged since it was captured (kernel_source_hash); else None."""
     try:
         text = open(os.path.join(ROOT, "profiles", "launches_ragged4096_pipeline.md")).read()
         vals = dict(line.split(":", 1) for line in text.splitlines()
                     if line.startswith(("pcg_traffic_bytes_per_solve:", "source_sha256_16:")))
-        h = hashlib.sha256()
-        for f in ("pcg.cuh", "kernels.h"):
-            with open(os.path.join(ROOT, "paper_2309_06427_gb300", "csrc", f), "rb") as fh:
-                h.update(fh.read())
-        if h.hexdigest()[:16] != vals["source_sha256_16"].strip():
+        if kernel_source_hash() != vals["source_sha256_16"].strip():
             return None
         return int(vals["pcg_traffic_bytes_per_solve"])
     except (OSError, KeyError, ValueError):

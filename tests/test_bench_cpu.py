@@ -34,8 +34,12 @@ def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.pcg_traffic() == int(open(os.path.join(root, "profiles", "launches_ragged4096_pipeline.md"))
                                       .read().split("pcg_traffic_bytes_per_solve:")[1].split()[0])
+    # a comment does not change the kernel; code does
     with open(root / "paper_2309_06427_gb300" / "csrc" / "pcg.cuh", "a") as f:
-        f.write("\n// changed\n")
+        f.write("\n// a comment\n")
+    assert bench.pcg_traffic() is not None
+    with open(root / "paper_2309_06427_gb300" / "csrc" / "pcg.cuh", "a") as f:
+        f.write("\nnamespace sspcg { constexpr int kChanged = 1; }\n")
     assert bench.pcg_traffic() is None
 
 
