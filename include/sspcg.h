@@ -38,10 +38,11 @@
  * Vectors gamma, lambda: [N+1][nx].
  *
  * Limits: 1 <= nx <= SSPCG_MAX_NX, 0 <= nu <= SSPCG_MAX_NX, 0 <= N <= SSPCG_MAX_N.  The
- * single-problem solves and the batched block-form solve need the PCG vectors of a
- * problem to fit in one CTA's shared memory (about 7 (N+1) nx + 2 N nu floats, at most
- * about 56000), else they return SSPCG_ERR_UNSUPPORTED; the batched QP-form calls keep
- * such problems' vectors in a plan-owned global workspace instead.
+ * single-problem solves, the batched block-form solve and the allocation-free solve need
+ * the PCG vectors of a problem to fit in one CTA's shared memory (about
+ * 7 (N+1) nx + 2 N nu floats, at most about 56000), else they return
+ * SSPCG_ERR_UNSUPPORTED; the plan-based batched QP-form calls keep such problems'
+ * vectors in a plan-owned global workspace instead.
  *
  * Ownership and execution.  Every array argument is a device pointer owned
  * by the caller, 16-byte aligned, unless the parameter is documented as a
