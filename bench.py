@@ -196,7 +196,8 @@ class ClockSampler:
 
 def cpu_baseline(probs, target_s: float, tol: float):
     """The FP64 oracle (build + preconditioner + PCG per problem, OpenMP over problems) on the first
-    problems of the workload, growing the sample until it runs about ``target_s`` seconds."""
+    problems of the workload, growing the sample until it runs about ``target_s`` seconds; when the whole
+    workload takes less, it is solved in repeated passes (at most 50) for about ``target_s`` seconds."""
     from oracle import block
     cores = os.cpu_count() or 1
     m = min(64, len(probs))
@@ -205,9 +206,15 @@ def cpu_baseline(probs, target_s: float, tol: float):
         if dt >= target_s or m >= len(probs):
             break
         m = min(len(probs), max(m + 1, int(m * min(8.0, 1.2 * target_s / max(dt, 1e-3)))))
-    return {"value": m / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
-            "sample": f"first {m} of the {len(probs)} problems (FP64 Schur build, preconditioner and PCG)",
-            "seconds": dt}
+    passes = 1
+    if dt < target_s:
+        passes = min(50, max(2, int(np.ceil(target_s / max(dt, 1e-3)))))
+        dt = 0.0
+        for _ in range(passes):
+            dt += block.solve_batch(probs[:m], PRECOND, tol, nthreads=cores)[5]
+    what = f"first {m} of the {len(probs)} problems" + (f", {passes} passes" if passes > 1 else "")
+    return {"value": passes * m / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
+            "sample": what + " (FP64 Schur build, preconditioner and PCG)", "seconds": dt}
 
 
 def run_reference(args, world, rank):
