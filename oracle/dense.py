@@ -17,6 +17,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   Sec. IV (symmetric stair), Sec. III (additive stair), Eq. (jacobi).
 * ``cholesky_solve``: the exact solution of S x = gamma.
 * ``pcg``: textbook PCG on dense matrices (Saad, Alg. 9.1).
+* ``pcg_counts_under_reordering``: its iteration counts over symmetric
+  reorderings of one system (how far FP64 rounding fixes the count).
 * ``form_gamma``, ``recover_step``: the two outer steps of Eq. (schur), written
   densely: gamma = c - C G^-1 g and delta z = G^-1 (g - C^T lambda*), with the
   paper's lambda* = -mu (mu solves C G^-1 C^T mu = gamma).  ``kkt_solve``: the
@@ -142,6 +144,21 @@ def pcg(S, Minv, gamma, tol, max_iter, x0=None):
         rz = rz_new
         it += 1
     return x, it, np.linalg.norm(r) / gn
+
+
+def pcg_counts_under_reordering(S, Minv, gamma, tol, max_iter, count=64, seed=0):
+    """Iteration counts of the textbook PCG (``pcg``) on ``count`` symmetric reorderings of the same system:
+    P S P^T y = P gamma with the preconditioner P Phi^-1 P^T, P a seeded random permutation (the first one
+    the identity).  In exact arithmetic every reordering takes the same iterations, so the spread of the
+    counts is what FP64 rounding alone (the order of its sums) leaves undetermined.  Returns a sorted array."""
+    g = np.asarray(gamma, dtype=np.float64).ravel()
+    rng = np.random.default_rng(seed)
+    counts = []
+    for t in range(count):
+        perm = np.arange(g.size) if t == 0 else rng.permutation(g.size)
+        ix = np.ix_(perm, perm)
+        counts.append(pcg(S[ix], Minv[ix], g[perm], tol, max_iter)[1])
+    return np.sort(np.array(counts))
 
 
 def spectrum(Minv, S) -> np.ndarray:

@@ -3,11 +3,11 @@ the FP64 oracle on the same seeded inputs."""
 import numpy as np
 import torch
 
-from oracle import block
+from oracle import block, dense
 from paper_2309_06427_gb300 import sspcg
 
 # Parity bar: relative 2-norm error of lambda against the FP64 oracle, and
-# iteration counts within one.
+# iteration counts within one (iters_match).
 LAMBDA_RTOL = 1e-5
 ITER_TOL = 1
 # Problems of at most this many unknowns take the FP64 path in the pipeline
@@ -19,20 +19,49 @@ def is_tiny(p):
     return p.n * p.nx <= TINY_UNKNOWNS
 
 
-def iters_ok(it_gpu, it_oracle, fp32_tiny=False, unknowns=None, kind=None):
-    """Iteration parity.  FP32 on tiny problems cannot reproduce the finite termination of
-    FP64 CG on the clustered spectrum (Thm. 4.2): there it may take more iterations, bounded.
-    When CG exhausts the Krylov space (oracle iterations >= 80% of the unknowns), the last steps
-    are decided by rounding in any precision and summation order; there the bar is 5%.
-    Scalar Jacobi (the slowest baseline, kappa(Phi^-1 S) ~ 1e2..1e4) in FP32: FP32 rounding costs a
-    few percent more iterations than FP64 CG (up to 4.2% measured); there the bar is 5%."""
-    if kind == "jacobi" and not fp32_tiny:
-        return abs(it_gpu - it_oracle) <= max(ITER_TOL, 0.05 * it_oracle)
-    if fp32_tiny:
-        return it_oracle - ITER_TOL <= it_gpu <= 2 * it_oracle + 2
-    if unknowns is not None and it_oracle >= 0.8 * unknowns:
-        return abs(it_gpu - it_oracle) <= max(ITER_TOL, 0.05 * it_oracle)
-    return abs(it_gpu - it_oracle) <= ITER_TOL
+def reorder_window(p, kind="sym", tol=1e-6, S=None, count=64):
+    """(lo, hi): the fewest and most iterations the oracle's dense FP64 textbook PCG takes over ``count``
+    symmetric reorderings of the problem's system (S: the oracle's blocks of the system solved; default the
+    oracle's FP64 Schur blocks of ``p``).  Oracle only: no value from the CUDA path enters it."""
+    if S is None:
+        S = block.build_schur(p.A, p.B, p.qd, p.rd)
+    M = block.build_precond(S, kind)
+    n = S.d.shape[0] * S.d.shape[1]
+    c = dense.pcg_counts_under_reordering(S.dense(), M.dense(), p.gamma, tol, 10 * n,
+                                          count=count if n <= 3000 else 16)
+    return int(c[0]), int(c[-1])
+
+
+def iters_ok(it_gpu, it_oracle, window=None):
+    """Within one of the oracle's count, or of the range ``window`` = (lo, hi)."""
+    lo, hi = window if window is not None else (it_oracle, it_oracle)
+    return lo - ITER_TOL <= it_gpu <= hi + ITER_TOL
+
+
+def iters_match(it_gpu, it_oracle, p, kind="sym", tol=1e-6, S=None):
+    """Iteration parity: within one of the oracle's count.  Where FP64 arithmetic does not fix the count
+    (reordering the oracle's own sums changes it by more than one: ill-conditioned runs, scalar Jacobi), the
+    bar is one around the range of the reordered FP64 counts.  That range is only computed when the first
+    test fails, and it always contains the oracle's count, so it never narrows the bar."""
+    if iters_ok(it_gpu, it_oracle):
+        return True
+    lo, hi = reorder_window(p, kind, tol, S)
+    return iters_ok(it_gpu, it_oracle, (min(lo, it_oracle), max(hi, it_oracle)))
+
+
+def oracle_blocks32(p):
+    """The oracle's FP64 Schur blocks of ``p`` rounded to FP32 on the host: (D [N+1, nx, nx], E [N, nx, nx]
+    as float32, and the oracle BlockTridiag of exactly those values).  The block-form GPU calls take these as
+    inputs, so that the oracle solves the same FP32 system without reading anything the GPU computed."""
+    S = block.build_schur(p.A, p.B, p.qd, p.rd)
+    D32 = S.d.astype(np.float32)
+    E32 = S.l[1:].astype(np.float32) if p.N > 0 else np.zeros((0, p.nx, p.nx), np.float32)
+    d = D32.astype(np.float64)
+    l = np.zeros_like(d); u = np.zeros_like(d)
+    if p.N > 0:
+        l[1:] = E32
+        u[:-1] = np.transpose(E32, (0, 2, 1))
+    return D32, E32, block.BlockTridiag(d, l, u)
 
 
 def dev(a, dtype=torch.float32):
@@ -103,15 +132,3 @@ def gpu_solve_qp_f64(p, kind="sym", tol=1e-6, **kw):
 def gpu_solve_auto(p, kind="sym", tol=1e-6, **kw):
     """The precision the batched pipeline uses for this problem (FP64 when tiny)."""
     return gpu_solve_qp_f64(p, kind, tol, **kw) if is_tiny(p) else gpu_solve_qp(p, kind, tol, **kw)
-
-
-def blocks_to_oracle(p, D, E):
-    """FP32 GPU blocks as an oracle BlockTridiag (exact conversion to FP64)."""
-    n, m = p.n, p.nx
-    d = D.cpu().numpy()[:n * m * m].reshape(n, m, m).astype(np.float64)
-    l = np.zeros((n, m, m)); u = np.zeros((n, m, m))
-    if p.N > 0:
-        e = E.cpu().numpy()[:p.N * m * m].reshape(p.N, m, m).astype(np.float64)
-        l[1:] = e
-        u[:-1] = np.transpose(e, (0, 2, 1))
-    return block.BlockTridiag(d, l, u)

@@ -14,7 +14,7 @@ if torch.cuda.is_available():
     from paper_2309_06427_gb300 import build as _build
     _build.build()
     from paper_2309_06427_gb300 import sspcg
-    from _gpu_helpers import LAMBDA_RTOL, blocks_to_oracle, dev, is_tiny, iters_ok, rel
+    from _gpu_helpers import LAMBDA_RTOL, dev, is_tiny, iters_match, rel
 
 BLOCK_RTOL = 1e-6
 SHAPES = [(0, 3, 2), (1, 1, 1), (4, 3, 2), (7, 5, 0), (12, 9, 5), (20, 28, 14), (33, 17, 9), (64, 14, 7)]
@@ -90,25 +90,34 @@ def test_batched_full_build_and_solve_match_oracle():
         Eg = torch.from_numpy(Eh[off_e[i]:off_e[i] + max(p.N * m * m, 0)].copy())
         _check_blocks(p, Dg, Eg if p.N else torch.zeros(4), S)
     assert n_all[sspcg.ARRAY_RFULL] == sum((p.N * p.nu * p.nu + 3) // 4 * 4 for p in probs)
-    # block-form solve on these blocks (problems whose vectors fit in shared memory)
+    # block-form solve (problems whose vectors fit in shared memory) on the oracle's full-cost blocks rounded
+    # to FP32 on the host, against the oracle's PCG on the same FP32 blocks
+    So32 = []
+    for i, p in enumerate(probs):
+        S = block.build_schur_full(p.A, p.B, *QR[i])
+        d = S.d.astype(np.float32).astype(np.float64)
+        l = np.zeros_like(d); u = np.zeros_like(d)
+        if p.N:
+            l[1:] = S.l[1:].astype(np.float32)
+            u[:-1] = np.transpose(l[1:], (0, 2, 1))
+        So32.append(block.BlockTridiag(d, l, u))
+    D32 = torch.from_numpy(plan.pack(sspcg.ARRAY_DIAG, [S.d.astype(np.float32) for S in So32])).cuda()
+    E32 = torch.from_numpy(plan.pack(sspcg.ARRAY_OFF, [S.l[1:].astype(np.float32) for S in So32])).cuda()
     stp = torch.zeros(plan.nprob, dtype=torch.int32, device="cuda")
-    sspcg.sspcg_build_precond_batched(plan, "sym", b.D, b.E, b.PD, b.PE, stp)
+    sspcg.sspcg_build_precond_batched(plan, "sym", D32, E32, b.PD, b.PE, stp)
     lam = plan.empty(sspcg.ARRAY_VEC)
     it = torch.zeros(plan.nprob, dtype=torch.int32, device="cuda")
     rr = torch.zeros(plan.nprob, dtype=torch.float64, device="cuda")
     sts = torch.zeros(plan.nprob, dtype=torch.int32, device="cuda")
-    sspcg.sspcg_solve_batched(plan, b.D, b.E, b.PD, b.PE, b.dev["gamma"], lam, it, rr, sts)
+    sspcg.sspcg_solve_batched(plan, D32, E32, b.PD, b.PE, b.dev["gamma"], lam, it, rr, sts)
     torch.cuda.synchronize()
     assert (stp.cpu().numpy() == 0).all() and (sts.cpu().numpy() == 0).all()
     lams = plan.unpack(sspcg.ARRAY_VEC, lam, [p.gamma.shape for p in probs])
     itn = it.cpu().numpy()
     for i, p in enumerate(probs):
-        m = p.nx
-        Dg = b.D.cpu()[off_d[i]:off_d[i] + p.n * m * m]
-        Eg = b.E.cpu()[off_e[i]:off_e[i] + p.N * m * m] if p.N else torch.zeros(4)
-        So = blocks_to_oracle(p, Dg, Eg)
-        x, it_o, _, _, st_o = block.pcg(So, block.build_precond(So, "sym"), p.gamma, 1e-6)
-        assert st_o == 0 and iters_ok(itn[i], it_o, fp32_tiny=is_tiny(p), unknowns=p.n * p.nx), (i, itn[i], it_o)
+        x, it_o, _, _, st_o = block.pcg(So32[i], block.build_precond(So32[i], "sym"), p.gamma, 1e-6)
+        # FP32 block form: iteration counts compared above 192 unknowns (FP64 finite termination below)
+        assert st_o == 0 and (is_tiny(p) or iters_match(itn[i], it_o, p, S=So32[i])), (i, itn[i], it_o)
         assert rel(lams[i], x) <= LAMBDA_RTOL, (i, rel(lams[i], x))
         # against the FP64 system itself: the true residual of the FP32-block solution
         Sf = block.build_schur_full(p.A, p.B, *QR[i]).dense()

@@ -17,7 +17,7 @@ if torch.cuda.is_available():
     from paper_2309_06427_gb300 import build as _build
     _build.build()
     from paper_2309_06427_gb300 import sspcg
-    from _gpu_helpers import LAMBDA_RTOL, blocks_to_oracle, dev, gpu_precond, gpu_schur, gpu_solve_qp, iters_ok, rel
+    from _gpu_helpers import LAMBDA_RTOL, dev, gpu_precond, gpu_solve_qp, is_tiny, iters_match, iters_ok, oracle_blocks32, rel
 
 
 def _ragged():
@@ -43,7 +43,7 @@ def test_pipeline_polynomial_matches_oracle(kind, degree):
     it = b.iters.cpu().numpy(); st = b.status.cpu().numpy(); rr = b.relres.cpu().numpy()
     assert (st == 0).all() and (st_o == 0).all() and (rr <= 1e-6).all()
     for i, p in enumerate(probs):
-        assert iters_ok(it[i], it_o[i], unknowns=p.n * p.nx), (i, p.N, p.nx, it[i], it_o[i])
+        assert iters_match(it[i], it_o[i], p, kind), (i, p.N, p.nx, it[i], it_o[i])
         assert rel(lams[i], xs[i]) <= LAMBDA_RTOL, (i, rel(lams[i], xs[i]))
 
 
@@ -74,12 +74,12 @@ def test_single_solves_qp_and_block_form(degree):
     lam, it, rr, st = gpu_solve_qp(p, "sym", 1e-6, poly_degree=degree)
     assert st == 0 and st_o == 0 and rr <= 1e-6
     assert iters_ok(it, it_o) and rel(lam, x_o) <= LAMBDA_RTOL
-    # block form on the GPU's FP32 blocks, against the oracle on the same blocks (a ragged-batch problem)
+    # block form on the oracle's blocks rounded to FP32, against the oracle on the same blocks
     p = P.make_workload(P.RAGGED_BATCH_4096, count=4)[3]
-    _, D, E = gpu_schur(p)
+    D32, E32, Sb = oracle_blocks32(p)
+    D, E = dev(D32.ravel()), dev(E32.ravel())
     PD, PE, pst = gpu_precond(p, D, E, "sym")
     assert pst == 0
-    Sb = blocks_to_oracle(p, D, E)
     Mb = block.build_precond(Sb, "sym")
     xb_o, itb_o, _, _, _ = block.pcg(Sb, Mb, p.gamma, 1e-6, degree=degree)
     g = dev(p.gamma)
@@ -90,7 +90,7 @@ def test_single_solves_qp_and_block_form(degree):
     sspcg.sspcg_solve(p.N, p.nx, D, E, PD, PE, g, lb, sspcg.options(tol=1e-6, poly_degree=degree), it_t, rr_t, st_t)
     torch.cuda.synchronize()
     assert int(st_t.item()) == 0
-    assert iters_ok(int(it_t.item()), itb_o, unknowns=p.n * p.nx)
+    assert iters_ok(int(it_t.item()), itb_o)
     assert rel(lb.cpu().numpy()[:p.gamma.size].reshape(p.gamma.shape), xb_o) <= LAMBDA_RTOL
 
 
@@ -107,7 +107,7 @@ def test_global_workspace_vectors_with_polynomial():
     it = b.iters.cpu().numpy()
     assert (b.status.cpu().numpy() == 0).all()
     for i, p in enumerate(probs):
-        assert iters_ok(it[i], it_o[i], unknowns=p.n * p.nx), (i, it[i], it_o[i])
+        assert iters_ok(it[i], it_o[i]), (i, it[i], it_o[i])
         assert rel(lams[i], xs[i]) <= LAMBDA_RTOL
 
 
@@ -133,5 +133,6 @@ def test_noalloc_solve_with_polynomial():
     itn = it.cpu().numpy()
     assert (st.cpu().numpy() == 0).all()
     for i, p in enumerate(probs):
-        assert iters_ok(itn[i], it_o[i], unknowns=p.n * p.nx)
+        # every problem runs in FP32 here: iteration counts compared above 192 unknowns
+        assert is_tiny(p) or iters_match(itn[i], it_o[i], p), (i, itn[i], it_o[i])
         assert rel(got[i], xs[i]) <= LAMBDA_RTOL

@@ -272,3 +272,30 @@ def test_batch_driver_matches_single_problem_path():
         _, _, x, it, rr, _, st = block.solve_problem(p, "sym", 1e-9)
         assert status[i] == st and iters[i] == it
         assert np.array_equal(xs[i], x)
+
+
+def test_pcg_counts_under_reordering():
+    """The reorder ensemble: the identity ordering reproduces the dense PCG's count, every reordering solves
+    the same system (same solution), a well-conditioned run is fixed to one count, and an ill-conditioned
+    scalar-Jacobi run is not (FP64 rounding alone moves its count by more than one)."""
+    from paper_2309_06427_gb300 import problems as P
+    p = P.make_workload(P.PENDULUM_SINGLE)[0]
+    S = block.build_schur(p.A, p.B, p.qd, p.rd)
+    M = block.build_precond(S, "sym")
+    g = p.gamma.ravel()
+    c = dense.pcg_counts_under_reordering(S.dense(), M.dense(), g, 1e-8, 1000, count=8)
+    _, it_d, _ = dense.pcg(S.dense(), M.dense(), g, 1e-8, 1000)
+    _, it_b, _, _, _ = block.pcg(S, M, p.gamma, 1e-8)
+    assert c[0] == c[-1] == it_d == it_b
+    perm = np.random.default_rng(3).permutation(g.size)
+    ix = np.ix_(perm, perm)
+    x_p, _, _ = dense.pcg(S.dense()[ix], M.dense()[ix], g[perm], 1e-12, 1000)
+    x, _, _ = dense.pcg(S.dense(), M.dense(), g, 1e-12, 1000)
+    assert np.allclose(x_p, x[perm], rtol=1e-9, atol=1e-12)
+    shapes = [(0, 1, 1), (0, 5, 3), (1, 2, 1), (2, 3, 2), (7, 4, 2), (20, 2, 1), (33, 12, 6), (64, 14, 7),
+              (17, 21, 11), (9, 28, 14), (40, 5, 1)]
+    q = P.custom_problems(shapes, h=0.05, config=55)[-1]
+    Sq = block.build_schur(q.A, q.B, q.qd, q.rd)
+    cj = dense.pcg_counts_under_reordering(Sq.dense(), block.build_precond(Sq, "jacobi").dense(), q.gamma.ravel(),
+                                           1e-6, 10000, count=64)
+    assert cj[-1] - cj[0] > 1
