@@ -157,6 +157,18 @@ const char *sspcg_last_cuda_error(void);
 /* Library version string. */
 const char *sspcg_version(void);
 
+/*
+ * Diagnostic (no counterpart in the paper): measured shared-memory read
+ * bandwidth of the current device, the peak the PCG kernel's roofline is
+ * reported against.  Two 1024-thread CTAs per SM read a 48 KB shared buffer
+ * ``rounds`` times with conflict-free loads of ``load_bytes`` (4 or 16)
+ * bytes; *gbytes_per_s = bytes read / kernel time (CUDA events, after one
+ * warm-up launch).  Synchronises ``stream``; allocates a small device buffer.
+ * Errors: SSPCG_ERR_INVALID_ARG for other sizes or rounds <= 0.
+ */
+sspcg_status sspcg_measure_smem_bandwidth(int32_t load_bytes, int32_t rounds, double *gbytes_per_s,
+                                          sspcg_stream stream);
+
 /* ------------------------------------------------------------------ */
 /* Single problem                                                     */
 /* ------------------------------------------------------------------ */
@@ -368,6 +380,50 @@ sspcg_status sspcg_plan_capture_pipeline(sspcg_plan *plan, sspcg_precond kind, c
 sspcg_status sspcg_plan_launch(sspcg_plan *plan, sspcg_stream stream);
 
 /*
+ * Autotuner (the batched schedule of Sec. II-B's PCG; the paper fixes no
+ * parallel schedule).  Builds the blocks and preconditioner like
+ * sspcg_pipeline_batched, then, for every PCG launch group of the chosen
+ * sets (which: SSPCG_TUNE_PIPELINE, the pipeline's FP32 and FP64 sets;
+ * SSPCG_TUNE_SOLVE, the set of sspcg_solve_qp_batched; or both; one group
+ * per nx and residency class), times candidate schedules alone on these
+ * inputs: block sizes 64..512 threads (16 rows per thread to one) and,
+ * for groups that do not fit in shared memory whole, staging the first rows
+ * or streaming every block row from L2.  Each group keeps its fastest
+ * candidate (grid from the kernel's occupancy at that block size); the
+ * choices also go to a process-wide cache keyed by (launch set, operator form,
+ * precision, reduction, polynomial degree, PCG variant, nx, residency class,
+ * bucket of the largest N: <16, <32, ..., <512, >=512), which later
+ * sspcg_plan_create calls with block_threads = 0 and the automatic schedule
+ * apply to matching groups.  Costs about 30 launches of each group.
+ * Arguments as sspcg_pipeline_batched; lambda, iters and relres are
+ * overwritten (a warm start is not used while tuning); status holds the
+ * preconditioner's codes afterwards.  A captured pipeline graph is dropped
+ * (capture again).  Synchronises ``stream``.
+ */
+#define SSPCG_TUNE_PIPELINE 1
+#define SSPCG_TUNE_SOLVE 2
+sspcg_status sspcg_plan_autotune(sspcg_plan *plan, int32_t which, sspcg_precond kind, const float *A, const float *B,
+                                 const float *qd, const float *rd, const float *gamma, float *D, float *E, float *PD,
+                                 float *PE, float *lambda, int32_t *iters, double *relres, int32_t *status,
+                                 sspcg_stream stream);
+
+/* Fields per group of sspcg_plan_schedule. */
+#define SSPCG_SCHEDULE_FIELDS 9
+/*
+ * The PCG launch groups of a plan: which = 0 (the pipeline's FP32 set),
+ * 1 (its FP64 set), 2 (sspcg_solve_qp_batched).  *count = number of groups;
+ * the first min(capacity, count) rows of SSPCG_SCHEDULE_FIELDS int32 go to
+ * out: nx, residency class (0 partially staged, 1..4 fully staged, 5
+ * vectors in global memory), problems, largest N, block threads, grid CTAs,
+ * dynamic shared memory bytes, streams every block row (0/1), chosen by the
+ * tuner or its cache (0/1).
+ */
+sspcg_status sspcg_plan_schedule(const sspcg_plan *plan, int32_t which, int32_t *out, int32_t capacity,
+                                 int32_t *count);
+/* Forget every cached tuning choice. */
+sspcg_status sspcg_autotune_cache_clear(void);
+
+/*
  * sspcg_pipeline_batched from HOST buffers (packed like the device arrays):
  * copies the inputs to plan-owned device buffers (allocated on first use),
  * runs the path, copies lambda, iters, relres and status back and waits for
@@ -426,13 +482,25 @@ sspcg_status sspcg_plan_join(sspcg_plan *plan, sspcg_stream stream);
  * Scratch: problem descriptors, the work list and work-queue counters live
  * in one file-scope __device__ array of 311,552 bytes (4096 descriptors),
  * which every GPU that loads the library holds until the process exits.
- * Each call copies its descriptors there with cudaMemcpyAsync from host
- * memory and clears the counters on ``stream``; all calls share the array,
- * so calls that overlap on the GPU (on different streams without ordering)
- * race and give wrong results.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  No cudaMalloc, cudaFree or allocating library routine
- * is called.
+ * All calls share the array, so calls that overlap on the GPU (on different
+ * streams without ordering) race and give wrong results.  No cudaMalloc,
+ * cudaFree or allocating library routine is called, and no host heap is
+ * used (about 25 KB of the calling thread's stack).
+ *
+ * Host behaviour: the call copies nothing with cudaMemcpy.  The shapes and
+ * the work order travel as the parameter block of one set-up kernel (the
+ * driver copies launch parameters when it records the launch), which writes
+ * the descriptors into the array and clears the queue counters and
+ * ``status`` on ``stream``; then one PCG launch per nx follows.  The call
+ * returns without waiting for the GPU.
+ *
+ * Warm-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make it before any stream capture.  The first
+ * launch of each PCG kernel variant (each nx and each reduction, schedule or
+ * CG option) sets that kernel's shared-memory attribute and, under lazy
+ * module loading, may load its code.  Callers with a time bound (a control
+ * loop) should make one call per nx and option set they will use before the
+ * loop starts; later calls do neither.
  */
 sspcg_status sspcg_solve_qp_batched_noalloc(int32_t nprob, const int32_t *N, const int32_t *nx, const int32_t *nu,
                                             const float *A, const float *B, const float *qd, const float *rd,
@@ -511,6 +579,22 @@ sspcg_status sspcg_mlp_set_params(sspcg_mlp *mlp, const float *params, sspcg_str
 /* Copy the FP32 parameters (or the gradients of the last training step) to a device array. */
 sspcg_status sspcg_mlp_get_params(const sspcg_mlp *mlp, float *params, sspcg_stream stream);
 sspcg_status sspcg_mlp_get_grads(const sspcg_mlp *mlp, float *grads, sspcg_stream stream);
+
+/*
+ * Checkpoint of a network for bit-exact resumption of training (no
+ * counterpart in the paper; the warm start is this library's addition):
+ * the FP32 parameters (masters), Adam's first and second moments, the Adam
+ * step count and the feature normalisation, in a versioned blob in HOST
+ * memory of sspcg_mlp_checkpoint_bytes() bytes, owned by the caller.  The
+ * bf16 weight copies are derived from the masters on load.  Both calls
+ * synchronise ``stream``.  Resuming from a checkpoint on the same GPU gives
+ * the same parameters, bit for bit, as training without the interruption.
+ * Errors: SSPCG_ERR_INVALID_ARG for a short buffer, or on load for a blob
+ * whose magic, version or layer sizes differ.
+ */
+sspcg_status sspcg_mlp_checkpoint_bytes(int64_t *bytes);
+sspcg_status sspcg_mlp_save(const sspcg_mlp *mlp, void *host_buf, int64_t bytes, sspcg_stream stream);
+sspcg_status sspcg_mlp_load(sspcg_mlp *mlp, const void *host_buf, int64_t bytes, sspcg_stream stream);
 /* Per-column normalisation (device arrays of SSPCG_MLP_IN floats). */
 sspcg_status sspcg_mlp_set_normalisation(sspcg_mlp *mlp, const float *mu, const float *inv_sigma,
                                          sspcg_stream stream);

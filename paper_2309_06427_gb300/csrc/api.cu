@@ -1,9 +1,12 @@
 // C ABI of sspcg: argument validation, batch plans, schedules and launches.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -31,27 +34,26 @@ sspcg_status cuda_fail(cudaError_t e) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-int device_sms() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
+// Device attribute of the current device, cached per device (devices beyond 63 query every time).
+int device_attr(cudaDeviceAttr what, std::atomic<int> (&cache)[64], int fallback) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
   }
-  return sms;
-}
-
-int max_smem_optin() {
-  static int v = 0;
-  if (v == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (v <= 0) v = 48 * 1024;
-  }
+  int v = 0;
+  if (dev < 0 || cudaDeviceGetAttribute(&v, what, dev) != cudaSuccess || v <= 0) v = fallback;
+  if (cached) cache[dev].store(v, std::memory_order_relaxed);
   return v;
 }
+
+std::atomic<int> g_sms[64], g_smem_optin[64];
+
+int device_sms() { return device_attr(cudaDevAttrMultiProcessorCount, g_sms, 1); }
+
+int max_smem_optin() { return device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, g_smem_optin, 48 * 1024); }
 
 // Static shared memory of the PCG kernels (reduction slots and the work index).
 constexpr int kPcgStaticSmem = 4 * 32 * 8 + 16;
@@ -94,7 +96,7 @@ bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int poly, int c
   // A problem that does not fit whole stages its first k block rows and streams the rest.  (Streaming
   // everything wins on a uniform batch of large problems, where it has the L2 bandwidth to itself, but
   // loses on the ragged batch, where the concurrent groups share it.)
-  if (sched == SSPCG_SCHED_STREAM) k = 0;
+  if (sched == SSPCG_SCHED_STREAM && N > 0) k = 0;  // a single knot stays staged (see pcg_layout)
   *K = k;
   *bytes = pcg_layout(op, k, N, nx, nu, poly > 0, cg).total * esz;
   return true;
@@ -151,21 +153,29 @@ constexpr int64_t kTinyUnknowns = 192;
 
 struct PcgGroup {
   int nx = 0;
+  int cls = 0;               // residency class (see plan_groups)
   bool resident = false;
   bool f64 = false;
   bool gvec = false;         // vectors in a global workspace (slot_elems per CTA from scratch_off)
+  bool stream = false;       // stage no block rows (the schedule option, or the tuner's choice)
+  bool tuned = false;        // block and residency from the tuner (this plan's, or its cache)
   int64_t slot_elems = 0, scratch_off = 0;
+  int max_grid = 0;          // global-vector groups: CTAs the workspace holds
   int block = 0;
   int grid = 0;
   size_t smem = 0;
   int32_t *d_work = nullptr;  // slice of the plan's work array
   int32_t nwork = 0;
   int counter_index = 0;
+  int32_t maxN = 0;
+  int64_t maxrows = 0;
+  std::vector<int32_t> members;  // indices into the set's descriptors, in work-list order
   double work = 0.0;  // estimated PCG work: sum over members of (N+1)^1.5 nx (3 nx + nu)
 };
 
 // A set of problems solved by one group of PCG launches (one per nx and schedule).
 struct GroupSet {
+  int id = 0;  // which set of the plan (the tuning cache keeps each set's choices apart)
   int op = kOpQp;
   bool f64 = false;
   std::vector<PcgGroup> groups;
@@ -288,6 +298,70 @@ void plan_free(sspcg_plan *p) {
   delete p;
 }
 
+// Tuning cache: the block size and residency the tuner picked, per (operator form, precision, reduction,
+// polynomial degree, PCG variant, nx, residency class, bucket of the group's largest N).  Process-wide; plans
+// created after a tuning run take its choices for groups with the same key.
+struct TuneKey {
+  int set, op, f64, red, poly, cg, nx, cls, nbucket;
+  bool operator<(const TuneKey &o) const {
+    const int a[9] = {set, op, f64, red, poly, cg, nx, cls, nbucket};
+    const int b[9] = {o.set, o.op, o.f64, o.red, o.poly, o.cg, o.nx, o.cls, o.nbucket};
+    return std::lexicographical_compare(a, a + 9, b, b + 9);
+  }
+};
+struct TuneChoice {
+  int block;
+  bool stream;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+int n_bucket(int32_t maxN) {
+  int b = 0;
+  while (b < 6 && maxN >= (16 << b)) ++b;  // <16, <32, <64, <128, <256, <512, >= 512
+  return b;
+}
+
+TuneKey tune_key(const sspcg_plan *p, const GroupSet &set, const PcgGroup &g) {
+  return TuneKey{set.id, set.op, set.f64 ? 1 : 0, set.f64 ? kRedF64 : red_mode(p->opts.reduction), p->opts.poly_degree,
+                 (p->opts.cg_variant && set.op == kOpQp && !set.f64) ? 1 : 0, g.nx, g.cls, n_bucket(g.maxN)};
+}
+
+// Dynamic shared memory, slot size and grid of a group for its block size and residency: every member's
+// layout (K = 0 when streaming), CTAs per SM from the kernel's occupancy (registers, threads, shared memory).
+sspcg_status shape_group(const sspcg_plan *p, const GroupSet &set, PcgGroup &g, const std::vector<ProbDesc> &descs) {
+  const int cg = set.f64 ? 0 : p->opts.cg_variant;
+  const int red = set.f64 ? kRedF64 : red_mode(p->opts.reduction);
+  int64_t maxbytes = 0;
+  for (int32_t i : g.members) {
+    const ProbDesc &d = descs[i];
+    int K = 0;
+    int64_t b = 0;
+    if (g.gvec) {
+      b = gvec_slot(set.op, d.N, d.nx, d.nu, p->opts.poly_degree, cg);
+    } else {
+      const int sched = g.stream ? SSPCG_SCHED_STREAM : p->opts.schedule;
+      if (!pcg_fit(set.op, sched, d.N, d.nx, d.nu, set.f64, p->opts.poly_degree, cg, &K, &b)) return SSPCG_ERR_UNSUPPORTED;
+    }
+    maxbytes = std::max(maxbytes, b);
+  }
+  int ctas = 0;
+  const bool cgv = cg && set.op == kOpQp && !set.f64;
+  cudaError_t e = occupancy_pcg(g.nx, set.op, red, set.f64, g.gvec, cgv, g.block, g.gvec ? 0 : (size_t)maxbytes, &ctas);
+  if (e != cudaSuccess) return cuda_fail(e);
+  ctas = std::max(1, ctas);
+  if (g.gvec) {
+    g.smem = 0;
+    g.slot_elems = maxbytes;
+    g.grid = (int)std::min<int64_t>(g.nwork, (int64_t)std::min(ctas, 2) * device_sms());
+    g.grid = std::min(g.grid, g.max_grid);
+  } else {
+    g.smem = (size_t)maxbytes;
+    g.grid = (int)std::min<int64_t>(g.nwork, (int64_t)ctas * device_sms());
+  }
+  return SSPCG_OK;
+}
+
 // PCG launch groups of one set: its members grouped by (nx, residency), each
 // group's work list ordered largest first.  ``members`` index ``descs``.
 sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDesc> &descs,
@@ -308,7 +382,6 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
         set.unsupported = true;
         continue;
       }
-      bytes[i] = gvec_slot(set.op, d.N, d.nx, d.nu, p->opts.poly_degree, set.f64 ? 0 : p->opts.cg_variant);
       buckets[kClasses * d.nx + 5].push_back(i);
       continue;
     }
@@ -326,38 +399,47 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
       std::stable_sort(b.begin(), b.end(), [&](int32_t x, int32_t y) { return descs[x].N > descs[y].N; });
       PcgGroup g;
       g.nx = nx;
+      g.cls = r;
       g.resident = r != 0 && r != 5;
       g.gvec = r == 5;
       g.f64 = set.f64;
-      int64_t maxrows = 0, maxsmem = 0;
+      g.stream = p->opts.schedule == SSPCG_SCHED_STREAM;
+      g.members = b;
       for (int32_t i : b) {
         const ProbDesc &d = descs[i];
-        maxrows = std::max<int64_t>(maxrows, (int64_t)(d.N + 1) * d.nx);
-        maxsmem = std::max<int64_t>(maxsmem, bytes[i]);
+        g.maxrows = std::max<int64_t>(g.maxrows, (int64_t)(d.N + 1) * d.nx);
+        g.maxN = std::max(g.maxN, d.N);
         // bytes per iteration times iterations, which grow about as sqrt(N + 1)
         g.work += std::pow((double)(d.N + 1), 1.5) * d.nx * (3.0 * d.nx + d.nu);
       }
-      g.block = p->opts.block_threads > 0 ? p->opts.block_threads : auto_block(maxrows);
-      const int by_thr = std::max(1, 2048 / g.block);
+      g.block = p->opts.block_threads > 0 ? p->opts.block_threads : auto_block(g.maxrows);
+      g.nwork = (int32_t)b.size();
+      if (p->opts.block_threads == 0 && p->opts.schedule == SSPCG_SCHED_AUTO) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(tune_key(p, set, g));
+        if (it != g_tune_cache.end()) {
+          g.block = it->second.block;
+          g.stream = it->second.stream && r == 0;
+          g.tuned = true;
+        }
+      }
       if (g.gvec) {
         // two CTAs per SM at most: each holds a workspace slot (about 7 (N+1) nx values)
-        g.smem = 0;
-        g.slot_elems = maxsmem;
-        g.grid = (int)std::min<int64_t>((int64_t)b.size(), (int64_t)std::min(2, by_thr) * device_sms());
+        g.max_grid = (int)std::min<int64_t>((int64_t)b.size(), 2 * (int64_t)device_sms());
+        g.slot_elems = 0;
+        for (int32_t i : b)
+          g.slot_elems = std::max(g.slot_elems, gvec_slot(set.op, descs[i].N, descs[i].nx, descs[i].nu,
+                                                          p->opts.poly_degree, set.f64 ? 0 : p->opts.cg_variant));
         g.scratch_off = set.scratch_elems;
-        set.scratch_elems += (int64_t)g.grid * g.slot_elems;
-      } else {
-        g.smem = (size_t)maxsmem;
-        const int64_t per_sm_smem = 228 * 1024;
-        const int by_smem = (int)std::max<int64_t>(1, per_sm_smem / (maxsmem + kPcgStaticSmem + 1024));
-        g.grid = (int)std::min<int64_t>((int64_t)b.size(), (int64_t)std::min(by_smem, by_thr) * device_sms());
+        set.scratch_elems += (int64_t)g.max_grid * g.slot_elems;
       }
-      g.nwork = (int32_t)b.size();
+      sspcg_status s = shape_group(p, set, g, descs);
+      if (s != SSPCG_OK) return s;
       g.d_work = p->d_work + pos;
       g.counter_index = p->ngroups_total++;
       for (int32_t i : b) work_host[pos++] = i;
       (g.gvec ? set.n_gvec : g.resident ? set.n_resident : set.n_stream) += g.nwork;
-      set.groups.push_back(g);
+      set.groups.push_back(std::move(g));
     }
   }
   return SSPCG_OK;
@@ -420,6 +502,7 @@ sspcg_status launch_sets(sspcg_plan *p, std::initializer_list<SetLaunch> list, c
     a.nwork = g.nwork;
     a.counter = p->d_counters + g.counter_index;
     set_gvec(a, p, *all[i].set, g);
+    if (g.stream) a.max_resident = 0;
     cudaStream_t s = i == 0 ? st : p->side[i - 1];
     const int red = g.f64 ? kRedF64 : red_mode(p->opts.reduction);
     SSPCG_CUDA(launch_pcg(g.nx, all[i].set->op, red, g.f64, a, g.grid, g.block, g.smem, s));
@@ -679,6 +762,7 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     std::vector<int32_t> tiny_local(p->ntiny);
     std::iota(tiny_local.begin(), tiny_local.end(), 0);
     int32_t pos = 0;
+    for (int k = 0; k < kNumSets; ++k) p->sets[k].id = k;
     p->sets[kSetQpAll].op = kOpQp;
     p->sets[kSetBlockAll].op = kOpBlock;
     p->sets[kSetQpMain].op = kOpQp;
@@ -1033,6 +1117,151 @@ sspcg_status sspcg_plan_capture_pipeline(sspcg_plan *plan, sspcg_precond kind, c
 sspcg_status sspcg_plan_launch(sspcg_plan *plan, sspcg_stream stream) {
   if (!plan || !plan->graph) return SSPCG_ERR_INVALID_ARG;
   SSPCG_CUDA(cudaGraphLaunch(plan->graph, (cudaStream_t)stream));
+  return SSPCG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------
+namespace {
+
+// Time one group alone on ``st``: statuses restored and the work counter cleared before each launch; the
+// first launch warms, the best of the next two counts.
+sspcg_status time_group(sspcg_plan *p, const GroupSet &set, const PcgGroup &g, const PcgArgs &base,
+                        const int32_t *status0, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+  PcgArgs a = base;
+  a.work = g.d_work;
+  a.nwork = g.nwork;
+  a.counter = p->d_counters + g.counter_index;
+  set_gvec(a, p, set, g);
+  if (g.stream) a.max_resident = 0;
+  const int red = g.f64 ? kRedF64 : red_mode(p->opts.reduction);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    SSPCG_CUDA(cudaMemcpyAsync(a.status, status0, sizeof(int32_t) * p->nprob, cudaMemcpyDeviceToDevice, st));
+    SSPCG_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int32_t), st));
+    SSPCG_CUDA(cudaEventRecord(e0, st));
+    SSPCG_CUDA(launch_pcg(g.nx, set.op, red, g.f64, a, g.grid, g.block, g.smem, st));
+    SSPCG_CUDA(cudaEventRecord(e1, st));
+    SSPCG_CUDA(cudaEventSynchronize(e1));
+    float t = 0.0f;
+    SSPCG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    if (rep > 0) best = std::min(best, t);
+  }
+  *ms = best;
+  return SSPCG_OK;
+}
+
+// Every candidate (block size; for partially staged groups also streaming every block row) of every group of
+// one set, timed alone; the fastest is kept in the plan and in the process-wide cache.
+sspcg_status tune_set(sspcg_plan *p, GroupSet &set, const std::vector<ProbDesc> &descs, const PcgArgs &base,
+                      const int32_t *status0, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  static const int kBlocks[] = {64, 96, 128, 160, 192, 256, 320, 384, 448, 512};
+  for (PcgGroup &g : set.groups) {
+    const PcgGroup orig = g;
+    float best_ms = 0.0f;
+    sspcg_status s = time_group(p, set, g, base, status0, st, e0, e1, &best_ms);
+    if (s != SSPCG_OK) return s;
+    PcgGroup best = g;
+    // from at most 16 rows per thread to at most one
+    const int64_t max_block = std::max<int64_t>(64, round_up(g.maxrows, 32));
+    const int64_t min_block = std::min<int64_t>(max_block, g.maxrows / 16);
+    for (int stream = 0; stream <= (g.cls == 0 ? 1 : 0); ++stream) {
+      for (int blk : kBlocks) {
+        if (blk > max_block || blk < min_block || (blk == orig.block && (stream != 0) == orig.stream)) continue;
+        PcgGroup c = orig;
+        c.block = blk;
+        c.stream = stream != 0;
+        if ((s = shape_group(p, set, c, descs)) != SSPCG_OK) return s;
+        float ms = 0.0f;
+        if ((s = time_group(p, set, c, base, status0, st, e0, e1, &ms)) != SSPCG_OK) return s;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+    }
+    g = best;
+    g.tuned = true;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[tune_key(p, set, g)] = TuneChoice{g.block, g.stream};
+  }
+  return SSPCG_OK;
+}
+
+}  // namespace
+
+sspcg_status sspcg_plan_autotune(sspcg_plan *plan, int32_t which, sspcg_precond kind, const float *A, const float *B,
+                                 const float *qd, const float *rd, const float *gamma, float *D, float *E, float *PD,
+                                 float *PE, float *lambda, int32_t *iters, double *relres, int32_t *status,
+                                 sspcg_stream stream) {
+  if (!plan || kind < 0 || kind > 3 || which < 1 || which > 3) return SSPCG_ERR_INVALID_ARG;
+  if (plan->nprob == 0) return SSPCG_OK;
+  sspcg_status s = check_solve_args(plan, kOpQp, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters,
+                                    relres, status);
+  if (s != SSPCG_OK) return s;
+  if (!D || (plan->total_off > 0 && !E)) return SSPCG_ERR_INVALID_ARG;
+  if (!aligned16(qd) || !aligned16(D)) return SSPCG_ERR_INVALID_ARG;
+  // the launch parameters change: a captured pipeline has to be captured again
+  if (plan->graph) {
+    cudaGraphExecDestroy(plan->graph);
+    plan->graph = nullptr;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool timing = plan->timing;
+  plan->timing = false;
+  s = pipeline_build(plan, kind, A, B, qd, rd, D, E, PD, PE, status, stream);
+  plan->timing = timing;
+  if (s != SSPCG_OK) return s;
+  int32_t *status0 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&status0, sizeof(int32_t) * plan->nprob);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(status0, status, sizeof(int32_t) * plan->nprob, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    PcgArgs a32 = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
+    a32.warm = 0;
+    PcgArgs a64 = a32;
+    a64.ps = tiny_set(plan);
+    a64.PD = plan->PD64;
+    a64.PE = plan->PE64;
+    if (which & SSPCG_TUNE_PIPELINE) {
+      s = tune_set(plan, plan->sets[kSetQpMain], plan->hdesc, a32, status0, st, e0, e1);
+      if (s == SSPCG_OK) s = tune_set(plan, plan->sets[kSetTiny], plan->tdesc, a64, status0, st, e0, e1);
+    }
+    if (s == SSPCG_OK && (which & SSPCG_TUNE_SOLVE))
+      s = tune_set(plan, plan->sets[kSetQpAll], plan->hdesc, a32, status0, st, e0, e1);
+    if (s == SSPCG_OK) e = cudaMemcpyAsync(status, status0, sizeof(int32_t) * plan->nprob, cudaMemcpyDeviceToDevice, st);
+    if (s == SSPCG_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(status0);
+  if (s != SSPCG_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e);
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_plan_schedule(const sspcg_plan *plan, int32_t which, int32_t *out, int32_t capacity,
+                                 int32_t *count) {
+  if (!plan || !count || which < 0 || which > 2 || capacity < 0 || (capacity > 0 && !out))
+    return SSPCG_ERR_INVALID_ARG;
+  const GroupSet &set = plan->sets[which == 0 ? kSetQpMain : which == 1 ? kSetTiny : kSetQpAll];
+  *count = (int32_t)set.groups.size();
+  const int32_t n = std::min<int32_t>(capacity, *count);
+  for (int32_t i = 0; i < n; ++i) {
+    const PcgGroup &g = set.groups[i];
+    int32_t *r = out + (int64_t)i * SSPCG_SCHEDULE_FIELDS;
+    r[0] = g.nx; r[1] = g.cls; r[2] = g.nwork; r[3] = g.maxN; r[4] = g.block; r[5] = g.grid;
+    r[6] = (int32_t)g.smem; r[7] = g.stream ? 1 : 0; r[8] = g.tuned ? 1 : 0;
+  }
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
   return SSPCG_OK;
 }
 

@@ -418,14 +418,10 @@ cudaError_t launch_schur_build(const ProbSet &ps, const int2 *refs, int64_t tota
                                cudaStream_t st, int sms, int mx) {
   if (total_knots == 0) return cudaSuccess;
   const size_t smem = sizeof(Real) * kBuildWarps * (4 * mx * mx + mx);
-  static bool attr = false;
-  if (!attr) {
-    const size_t most = sizeof(Real) * kBuildWarps * (4 * kMaxNx * kMaxNx + kMaxNx);
-    cudaError_t e =
-        cudaFuncSetAttribute(schur_build_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  const size_t most = sizeof(Real) * kBuildWarps * (4 * kMaxNx * kMaxNx + kMaxNx);
+  cudaError_t e = smem_attr_once(attr_done, schur_build_kernel<Real>, (int)most);
+  if (e != cudaSuccess) return e;
   schur_build_kernel<Real><<<build_grid(total_knots, sms), kBuildWarps * 32, smem, st>>>(ps, refs, total_knots,
                                                                                           A, B, qd, rd, D, E, mx);
   return cudaGetLastError();
@@ -436,13 +432,10 @@ cudaError_t launch_schur_full(const ProbSet &ps, const int2 *refs, int64_t total
                               cudaStream_t st, int mx) {
   if (total_knots == 0) return cudaSuccess;
   const size_t smem = sizeof(float) * kBuildWarps * 6 * mx * mx;
-  static bool attr = false;
-  if (!attr) {
-    const size_t most = sizeof(float) * kBuildWarps * 6 * kMaxNx * kMaxNx;
-    cudaError_t e = cudaFuncSetAttribute(schur_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  const size_t most = sizeof(float) * kBuildWarps * 6 * kMaxNx * kMaxNx;
+  cudaError_t e = smem_attr_once(attr_done, schur_full_kernel, (int)most);
+  if (e != cudaSuccess) return e;
   schur_full_kernel<<<build_grid(total_knots, 0), kBuildWarps * 32, smem, st>>>(ps, refs, total_knots, roff, A, B,
                                                                                  Qi, Ri, D, E, mx);
   return cudaGetLastError();
@@ -452,15 +445,10 @@ template <typename Real>
 cudaError_t launch_precond_inv(const ProbSet &ps, const int2 *refs, int64_t total_knots, int nx, int kind,
                                const Real *D, Real *PD, int32_t *status, cudaStream_t st) {
   if (total_knots == 0) return cudaSuccess;
-  static int attr_set = 0;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(precond_inv_kernel<Real, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         210 * 1024);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(precond_inv_kernel<Real, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = 1;
-  }
+  static std::atomic<uint64_t> attr4{0}, attr8{0};
+  cudaError_t e = smem_attr_once(attr4, precond_inv_kernel<Real, 4>, 210 * 1024);
+  if (e == cudaSuccess) e = smem_attr_once(attr8, precond_inv_kernel<Real, 8>, 210 * 1024);
+  if (e != cudaSuccess) return e;
   // lanes per knot: 8 for the larger blocks, 4 otherwise; knots per CTA limited by 200 KB of shared memory
   const int G = nx >= 16 ? 8 : 4;
   const int per_knot = (inv_stride(nx) + nx) * (int)sizeof(double);
@@ -485,14 +473,10 @@ cudaError_t launch_precond_off(const ProbSet &ps, const int2 *refs, int64_t tota
     return cudaMemsetAsync(PE, 0, sizeof(Real) * off_elems, st);
   }
   const size_t smem_o = sizeof(Real) * kBuildWarps * (4 * mx * mx);
-  static bool attr = false;
-  if (!attr) {
-    const size_t most = sizeof(Real) * kBuildWarps * (4 * kMaxNx * kMaxNx);
-    cudaError_t e =
-        cudaFuncSetAttribute(precond_off_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  const size_t most = sizeof(Real) * kBuildWarps * (4 * kMaxNx * kMaxNx);
+  cudaError_t e = smem_attr_once(attr_done, precond_off_kernel<Real>, (int)most);
+  if (e != cudaSuccess) return e;
   const Real c = (kind == 0) ? Real(1) : Real(0.5);
   precond_off_kernel<Real><<<build_grid(total_off, sms), kBuildWarps * 32, smem_o, st>>>(ps, refs, total_off, c,
                                                                                           E, PD, PE, mx);

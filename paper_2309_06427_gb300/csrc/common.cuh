@@ -1,6 +1,7 @@
 // Shared device-side definitions of the sspcg CUDA library (sm_103a).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -142,6 +143,20 @@ __device__ __forceinline__ int find_problem(const int64_t *knot_start, int nprob
     if (knot_start[mid] <= g) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Host: set a kernel's largest dynamic shared memory once per device.  Bit d
+// of ``done`` records device d; devices beyond 63 set it on every call.
+template <typename Kern>
+inline cudaError_t smem_attr_once(std::atomic<uint64_t> &done, Kern kernel, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev >= 0 && dev < 64 ? (uint64_t{1} << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 }  // namespace sspcg

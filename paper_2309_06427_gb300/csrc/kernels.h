@@ -22,8 +22,16 @@ __host__ __device__ __forceinline__ int pad_ld(int x) { return x | 1; }
 // the operator and preconditioner blocks are staged (K = N+1: fully
 // resident; K = 0: everything read from L2/HBM each iteration).  The same
 // function sizes launches on the host and carves on the device.
+//
+// Every vector has a zero segment before block row 0 and after block row N
+// (the offsets below point at block row 0), so that a row's three block
+// products read their neighbour segments without branches: the segment of
+// the missing neighbour is zero.  A single-knot problem (N = 0) stages one
+// zero off-diagonal slot, so that its clamped off-diagonal reads stay in
+// bounds.
 struct PcgLayout {
   int64_t p, r, w, x, e, u, s, v;   // vectors (e: the polynomial's residual; u, s: single-reduction CG)
+  int64_t vu;                       // v_u block rows (QP form), after v_x
   int64_t iq, ir;                   // 1/q, 1/r (QP form)
   int64_t m0, m1, pd, pe;           // staged blocks
   int64_t total;
@@ -34,26 +42,34 @@ struct PcgLayout {
 // whole block-row segment with 128-bit loads.
 __host__ __device__ __forceinline__ int vec_stride(int x) { return (x + 3) & ~3; }
 
+// Staged off-diagonal slots of a layout with K staged block rows: K (at most N), and one zero slot for N = 0.
+__host__ __device__ __forceinline__ int64_t staged_off_slots(int K, int N) {
+  const int64_t Ks = K < N ? K : N;
+  return (N == 0 && K > 0) ? 1 : Ks;
+}
+
 __host__ __device__ inline PcgLayout pcg_layout(int op, int K, int N, int nx, int nu, int poly = 0, int cg = 0) {
   PcgLayout L{};
-  const int64_t n = N + 1, NXP = vec_stride(nx), NUP = vec_stride(nu), RV = n * NXP;
-  const int64_t Ks = K < N ? K : N;  // staged off-diagonal slots
+  const int64_t n = N + 1, NXP = vec_stride(nx), NUP = vec_stride(nu);
+  const int64_t RVP = (n + 2) * NXP;  // a vector with its two zero segments
+  const int64_t Ks = staged_off_slots(K, N);
   const int64_t ld = pad_ld(nx), ldb = pad_ld(nu > 0 ? nu : 1);
   int64_t o = 0;
-  L.p = o; o += RV;
-  L.r = o; o += RV;
-  L.w = o; o += RV;
-  L.x = o; o += RV;
-  L.e = o;
-  if (poly) o += RV;
-  L.u = o;
-  if (cg) o += RV;
-  L.s = o;
-  if (cg) o += RV;
-  L.v = o;
-  if (op == kOpQp) o += RV + (int64_t)N * NUP;   // v_x then v_u
+  L.p = o + NXP; o += RVP;
+  L.r = o + NXP; o += RVP;
+  L.w = o + NXP; o += RVP;
+  L.x = o + NXP; o += RVP;
+  L.e = o + NXP;
+  if (poly) o += RVP;
+  L.u = o + NXP;
+  if (cg) o += RVP;
+  L.s = o + NXP;
+  if (cg) o += RVP;
+  L.v = o + NXP;  // the block form has no v (no region)
+  L.vu = op == kOpQp ? L.v + (n + 1) * NXP + NUP : L.v;
+  if (op == kOpQp) o += RVP + (int64_t)(N + 1) * NUP;   // v_x with its zero segments, then v_u after one
   L.iq = o;
-  if (op == kOpQp) o += RV;
+  if (op == kOpQp) o += n * NXP;
   L.ir = o;
   if (op == kOpQp) o += (int64_t)N * NUP;
   if (op == kOpQp) {
@@ -115,6 +131,9 @@ struct PcgArgs {
 cudaError_t launch_pcg(int nx, int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
                        cudaStream_t st);
 int pcg_max_smem_bytes();
+// CTAs of that PCG variant that fit on one SM at ``block`` threads and ``smem`` bytes of dynamic shared memory
+// (registers, threads and shared memory; gv: vectors in a global workspace; cg: single-reduction PCG).
+cudaError_t occupancy_pcg(int nx, int op, int red, bool f64, bool gv, bool cg, int block, size_t smem, int *ctas);
 
 // Schur build and preconditioner assembly; Real = float (FP32 blocks) or
 // double (the FP64 path).  refs[i] = (problem, block row) of work item i

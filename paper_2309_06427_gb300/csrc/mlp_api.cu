@@ -2,6 +2,7 @@
 // normalisation, inference, one training step, and the warm-started pipeline.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "../../include/sspcg.h"
@@ -316,6 +317,72 @@ sspcg_status sspcg_mlp_train_step(sspcg_mlp *n, const sspcg_plan *plan, int32_t 
   a.update = 1;
   a.W1b = n->W1b; a.W2b = n->W2b; a.W3b = n->W3b; a.W2t = n->W2t; a.W3t = n->W3t;
   MLP_CUDA(launch_adam(a, st));
+  return SSPCG_OK;
+}
+
+// Checkpoint blob: a header, then the FP32 parameters (the masters), Adam's first and second moments, and
+// the feature normalisation (mu, 1/sigma).  The bf16 weight copies are derived from the masters.
+namespace {
+struct CkptHeader {
+  char magic[8];  // "SSPCGMLP"
+  int32_t version, in, hidden, out;
+  int64_t params, steps;
+};
+constexpr int32_t kCkptVersion = 1;
+constexpr int64_t kCkptBytes = (int64_t)sizeof(CkptHeader) + 3 * kParams * (int64_t)sizeof(float) +
+                               2 * (int64_t)kIn * (int64_t)sizeof(float);
+}  // namespace
+
+sspcg_status sspcg_mlp_checkpoint_bytes(int64_t *bytes) {
+  if (!bytes) return SSPCG_ERR_INVALID_ARG;
+  *bytes = kCkptBytes;
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_mlp_save(const sspcg_mlp *n, void *host_buf, int64_t bytes, sspcg_stream stream) {
+  if (!n || !host_buf || bytes < kCkptBytes) return SSPCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CkptHeader h{};
+  std::memcpy(h.magic, "SSPCGMLP", 8);
+  h.version = kCkptVersion; h.in = kIn; h.hidden = kHid; h.out = kOut; h.params = kParams; h.steps = n->t;
+  char *b = static_cast<char *>(host_buf);
+  std::memcpy(b, &h, sizeof(h));
+  char *cur = b + sizeof(h);
+  for (const float *src : {(const float *)n->w, (const float *)n->m, (const float *)n->v}) {
+    MLP_CUDA(cudaMemcpyAsync(cur, src, sizeof(float) * kParams, cudaMemcpyDeviceToHost, st));
+    cur += sizeof(float) * kParams;
+  }
+  for (const float *src : {(const float *)n->mu, (const float *)n->isd}) {
+    MLP_CUDA(cudaMemcpyAsync(cur, src, sizeof(float) * kIn, cudaMemcpyDeviceToHost, st));
+    cur += sizeof(float) * kIn;
+  }
+  MLP_CUDA(cudaStreamSynchronize(st));
+  return SSPCG_OK;
+}
+
+sspcg_status sspcg_mlp_load(sspcg_mlp *n, const void *host_buf, int64_t bytes, sspcg_stream stream) {
+  if (!n || !host_buf || bytes < kCkptBytes) return SSPCG_ERR_INVALID_ARG;
+  CkptHeader h;
+  const char *b = static_cast<const char *>(host_buf);
+  std::memcpy(&h, b, sizeof(h));
+  if (std::memcmp(h.magic, "SSPCGMLP", 8) != 0 || h.version != kCkptVersion || h.in != kIn || h.hidden != kHid ||
+      h.out != kOut || h.params != kParams || h.steps < 0)
+    return SSPCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const char *cur = b + sizeof(h);
+  for (float *dst : {n->w, n->m, n->v}) {
+    MLP_CUDA(cudaMemcpyAsync(dst, cur, sizeof(float) * kParams, cudaMemcpyHostToDevice, st));
+    cur += sizeof(float) * kParams;
+  }
+  for (float *dst : {n->mu, n->isd}) {
+    MLP_CUDA(cudaMemcpyAsync(dst, cur, sizeof(float) * kIn, cudaMemcpyHostToDevice, st));
+    cur += sizeof(float) * kIn;
+  }
+  MLP_CUDA(cudaMemsetAsync(n->g, 0, sizeof(float) * kParams, st));
+  n->t = h.steps;
+  sspcg_status s = refresh_copies(n, st);
+  if (s != SSPCG_OK) return s;
+  MLP_CUDA(cudaStreamSynchronize(st));
   return SSPCG_OK;
 }
 

@@ -261,13 +261,9 @@ template <int N, int EPI>
 cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int64_t M, int K, const float *bias, bf16 *Cb,
                       float *Cf, int *err, cudaStream_t st) {
   using C = TcCfg<N>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_nt_tc_kernel<N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         C::kSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t e = smem_attr_once(attr_done, gemm_nt_tc_kernel<N, EPI>, C::kSmem);
+  if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((M + kTcM - 1) / kTcM);
   gemm_nt_tc_kernel<N, EPI><<<grid, kTcThreads, C::kSmem, st>>>(ma, mb, M, K, bias, Cb, Cf, err);
   return cudaGetLastError();

@@ -135,22 +135,23 @@ __device__ __forceinline__ Real dot_seg(const MT *m, int stride, const Real *seg
 // stride NXP): Md diagonal blocks (symmetric; read by column so that
 // consecutive i are consecutive addresses), Mo sub-diagonal blocks with
 // Mo[k-1] = M(k, k-1) (read by row), and M(k, k+1) = Mo[k]^T (read by
-// column).  ld: row stride.
+// column).  ld: row stride.  The segments of v at block rows -1 and N + 1
+// are zero, so the three products run without branches and can overlap:
+// the off-diagonal block index is clamped into range (slot 0, a zero block,
+// when N = 0) and multiplies the zero segment at the ends.
 template <int NX, bool SMEM, typename Real, typename MT>
 __device__ __forceinline__ Real bt_row(const MT *Md, const MT *Mo, int ld, int N, int k, int i, const Real *v) {
   constexpr int NXP = (NX + 3) & ~3;
-  Seg<NX, Real> s;
-  s.load(v + k * NXP);
-  Real acc = dot_seg<NX, SMEM, Real>(Md + (int64_t)k * NX * ld + i, ld, s.v);
-  if (k > 0) {
-    s.load(v + (k - 1) * NXP);
-    acc += dot_seg<NX, SMEM, Real>(Mo + ((int64_t)(k - 1) * NX + i) * ld, 1, s.v);
-  }
-  if (k < N) {
-    s.load(v + (k + 1) * NXP);
-    acc += dot_seg<NX, SMEM, Real>(Mo + (int64_t)k * NX * ld + i, ld, s.v);
-  }
-  return acc;
+  Seg<NX, Real> s0, s1, s2;
+  s0.load(v + k * NXP);
+  s1.load(v + (k - 1) * NXP);
+  s2.load(v + (k + 1) * NXP);
+  const int km = k > 0 ? k - 1 : 0;
+  const int kp = k < N ? k : (N > 0 ? N - 1 : 0);
+  const Real a = dot_seg<NX, SMEM, Real>(Md + (int64_t)k * NX * ld + i, ld, s0.v);
+  const Real b = dot_seg<NX, SMEM, Real>(Mo + ((int64_t)km * NX + i) * ld, 1, s1.v);
+  const Real c = dot_seg<NX, SMEM, Real>(Mo + (int64_t)kp * NX * ld + i, ld, s2.v);
+  return (a + b) + c;
 }
 
 template <int NX, typename Real>
@@ -185,11 +186,23 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems, poly > 0, CG);  // the host sized smem so that K >= 0
   if (K > a.max_resident) K = a.max_resident;
   if (K < 0) K = 0;
+  if (N == 0) K = 1;  // a single knot is always staged, with its zero off-diagonal slot
   const int Ks = K < N ? K : N;
   const PcgLayout L = pcg_layout(OP, K, N, NX, nu, poly > 0, CG);
   Real *sp = sm + L.p, *sr = sm + L.r, *sw = sm + L.w, *sx = sm + L.x, *sv = sm + L.v, *se = sm + L.e;
   Real *su = sm + L.u, *ss = sm + L.s;
-  Real *svu = sv + n * NXP;  // v_u block rows, stride NUP
+  Real *svu = sm + L.vu;  // v_u block rows, stride NUP
+  // zero segments before block row 0 and after block row N of the vectors whose neighbour segments are read
+  for (int e = tid; e < NXP; e += T) {
+    sp[e - NXP] = Real(0); sp[n * NXP + e] = Real(0);
+    sr[e - NXP] = Real(0); sr[n * NXP + e] = Real(0);
+    sw[e - NXP] = Real(0); sw[n * NXP + e] = Real(0);
+    if (poly > 0) { se[e - NXP] = Real(0); se[n * NXP + e] = Real(0); }
+    if (CG) { su[e - NXP] = Real(0); su[n * NXP + e] = Real(0); }
+    if (OP == kOpQp) sv[e - NXP] = Real(0);
+  }
+  if (OP == kOpQp)
+    for (int e = tid; e < NUP; e += T) svu[e - NUP] = Real(0);
   const float *gam = a.gamma + d.ovec;
   // lambda (global): read once for a warm start, written once at the end
   auto lam_load = [&](int row) -> Real {
@@ -217,6 +230,8 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     Real *spd = sm + L.pd, *spe = sm + L.pe;
     stage_blocks<NX>(spd, V.gPD, K, V.ld, tid, T);
     stage_blocks<NX>(spe, V.gPE, Ks, V.ld, tid, T);
+    if (N == 0)  // the zero off-diagonal slot of a single knot
+      for (int e = tid; e < NX * V.ld; e += T) spe[e] = Real(0);
     V.sPD = spd; V.sPE = spe;
   }
   const float *gq = a.qd + d.oq, *gr = a.rd + d.orr;
@@ -232,6 +247,10 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     for (int e = tid; e < Ks * NX * nu; e += T) {
       const int row = e / nu, c = e - row * nu;
       s1[row * V.ldb + c] = (Real)V.gB[e];
+    }
+    if (N == 0) {  // the zero off-diagonal slot of a single knot
+      for (int e = tid; e < NX * V.ld; e += T) s0[e] = Real(0);
+      for (int e = tid; e < NX * V.ldb; e += T) s1[e] = Real(0);
     }
     for (int e = tid; e < R_; e += T) {
       const int k = e / NX, j = e - k * NX;
@@ -254,12 +273,15 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
       s1[(b * NX + r) * V.ld + c] = (Real)V.gE[e];
     }
+    if (N == 0)  // the zero off-diagonal slot of a single knot
+      for (int e = tid; e < NX * V.ld; e += T) s1[e] = Real(0);
     V.sD = s0; V.sE = s1;
   }
 
   // QP form, phase 1: sv = G^-1 C^T src (all threads), then a barrier.
   //   v_x(k)[j] = (-src_k[j] + sum_l A_k[l][j] src_{k+1}[l]) / q_k[j]
   //   v_u(k)[j] = (sum_l B_k[l][j] src_{k+1}[l]) / r_k[j]
+  // Branch-free at k = N: the block index is clamped and src_{N+1} is the zero segment.
   auto apply_S_phase1 = [&](const Real *src) {
     if constexpr (OP == kOpQp) {
       const int nitems = R_ + N * nu;
@@ -267,14 +289,12 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       for (int it = tid; it < nitems; it += T) {
         if (it < R_) {
           const int k = it / NX, j = it - k * NX;
-          Real acc = -src[k * NXP + j];
-          if (k < N) {
-            Seg<NX, Real> s;
-            s.load(src + (k + 1) * NXP);
-            if (k < K) acc += dot_seg<NX, true, Real>(V.sA + k * NX * V.ld + j, V.ld, s.v);
-            else acc += dot_seg<NX, false, Real>(V.gA + (int64_t)k * NX * NX + j, NX, s.v);
-          }
-          sv[k * NXP + j] = acc * siq[k * NXP + j];
+          const int kp = k < N ? k : (N > 0 ? N - 1 : 0);
+          Seg<NX, Real> s;
+          s.load(src + (k + 1) * NXP);
+          const Real ax = k < K ? dot_seg<NX, true, Real>(V.sA + kp * NX * V.ld + j, V.ld, s.v)
+                                : dot_seg<NX, false, Real>(V.gA + (int64_t)kp * NX * NX + j, NX, s.v);
+          sv[k * NXP + j] = (-src[k * NXP + j] + ax) * siq[k * NXP + j];
         } else {
           const int t2 = it - R_;
           const int k = (int)(((float)t2 + 0.5f) * inv_nu);
@@ -292,25 +312,26 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   };
   // Row (k, i) of S src (QP form: of C sv).
   //   w_k[i] = -v_x(k)[i] + A_{k-1}[i,:] v_x(k-1) + B_{k-1}[i,:] v_u(k-1)
+  // Branch-free at k = 0: the block index is clamped and v_x(-1), v_u(-1) are zero segments.
   auto apply_S_row = [&](const Real *src, int k, int i) -> Real {
     if constexpr (OP == kOpQp) {
+      const int km = k > 0 ? k - 1 : 0;
+      Seg<NX, Real> s;
+      s.load(sv + (k - 1) * NXP);
+      const Real *vu = svu + (k - 1) * NUP;
       Real acc = -sv[k * NXP + i];
-      if (k > 0) {
-        Seg<NX, Real> s;
-        s.load(sv + (k - 1) * NXP);
-        const Real *vu = svu + (k - 1) * NUP;
-        Real ab = Real(0);
-        if (k < K) {
-          acc += dot_seg<NX, true, Real>(V.sA + ((k - 1) * NX + i) * V.ld, 1, s.v);
-          const Real *Br = V.sB + ((k - 1) * NX + i) * V.ldb;
-          for (int j = 0; j < nu; ++j) ab = rfma(Br[j], vu[j], ab);
-        } else {
-          acc += dot_seg<NX, false, Real>(V.gA + ((int64_t)(k - 1) * NX + i) * NX, 1, s.v);
-          const float *Br = V.gB + ((int64_t)(k - 1) * NX + i) * nu;
-          for (int j = 0; j < nu; ++j) ab = rfma((Real)__ldg(Br + j), vu[j], ab);
-        }
-        acc += ab;
+      Real ax, ab = Real(0);  // one accumulator, j in order: the sum order the parity runs were made with
+      if (k < K) {
+        ax = dot_seg<NX, true, Real>(V.sA + (km * NX + i) * V.ld, 1, s.v);
+        const Real *Br = V.sB + (km * NX + i) * V.ldb;
+        for (int j = 0; j < nu; ++j) ab = rfma(Br[j], vu[j], ab);
+      } else {
+        ax = dot_seg<NX, false, Real>(V.gA + ((int64_t)km * NX + i) * NX, 1, s.v);
+        const float *Br = V.gB + ((int64_t)km * NX + i) * nu;
+        for (int j = 0; j < nu; ++j) ab = rfma((Real)__ldg(Br + j), vu[j], ab);
       }
+      acc += ax;
+      acc += ab;
       return acc;
     } else {
       return k < K ? bt_row<NX, true, Real>(V.sD, V.sE, V.ld, N, k, i, src)
@@ -594,47 +615,54 @@ __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
   }
 }
 
-template <int NX, int OP, int RED, typename Real, bool GV, bool CG = false>
-cudaError_t launch_variant(const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
-  auto k = pcg_kernel<NX, OP, RED, Real, GV, CG>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_max_smem_bytes());
+// One compiled variant of the PCG kernel: its launch and its occupancy (CTAs per SM for a block size and
+// dynamic shared memory, registers included).  The shared-memory attribute is set once per device.
+template <int NX, int OP, int RED, typename Real, bool GV, bool CG>
+struct PcgVariant {
+  static cudaError_t prepare() {
+    static std::atomic<uint64_t> attr_done{0};
+    return smem_attr_once(attr_done, pcg_kernel<NX, OP, RED, Real, GV, CG>, pcg_max_smem_bytes());
+  }
+  static cudaError_t launch(const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
+    cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
-    attr = true;
+    PcgArgs b = a;
+    b.smem_elems = (int64_t)(smem / sizeof(Real));
+    pcg_kernel<NX, OP, RED, Real, GV, CG><<<grid, block, smem, st>>>(b);
+    return cudaGetLastError();
   }
-  PcgArgs b = a;
-  b.smem_elems = (int64_t)(smem / sizeof(Real));
-  k<<<grid, block, smem, st>>>(b);
-  return cudaGetLastError();
-}
+  static cudaError_t occupancy(int block, size_t smem, int *ctas) {
+    cudaError_t e = prepare();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, pcg_kernel<NX, OP, RED, Real, GV, CG>, block, smem);
+  }
+};
 
-// All variants of one nx: FP32 with three reduction modes for both operator
-// forms, and the FP64 path (QP form, FP64 reductions); vectors in a global
-// workspace for the QP form only; single-reduction PCG for the QP form with
-// FP32 arithmetic and double-float sums.
-template <int NX>
-cudaError_t launch_pcg_for_nx(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
-                              cudaStream_t st) {
-  if (a.cg && op == kOpQp && !f64) {  // single-reduction PCG (the FP64 and block-form launches stay textbook)
+// The variant of one nx for an operator form, reduction mode and precision: FP32 with three reduction modes
+// for both operator forms, and the FP64 path (QP form, FP64 reductions); vectors in a global workspace (gv)
+// for the QP form only; single-reduction PCG (cg) for the QP form with FP32 arithmetic and double-float sums.
+// f(PcgVariant<...>{}) is called on it; cudaErrorInvalidValue when no variant exists.
+template <int NX, typename F>
+cudaError_t with_pcg_variant(int op, int red, bool f64, bool gv, bool cg, F &&f) {
+  if (cg && op == kOpQp && !f64) {  // single-reduction PCG (the FP64 and block-form launches stay textbook)
     if (red != kRedDf) return cudaErrorInvalidValue;
-    if (a.gscratch) return launch_variant<NX, kOpQp, kRedDf, float, true, true>(a, grid, block, smem, st);
-    return launch_variant<NX, kOpQp, kRedDf, float, false, true>(a, grid, block, smem, st);
+    if (gv) return f(PcgVariant<NX, kOpQp, kRedDf, float, true, true>{});
+    return f(PcgVariant<NX, kOpQp, kRedDf, float, false, true>{});
   }
-  if (a.gscratch) {
+  if (gv) {
     if (op != kOpQp) return cudaErrorInvalidValue;
-    if (f64) return launch_variant<NX, kOpQp, kRedF64, double, true>(a, grid, block, smem, st);
-    if (red == kRedDf) return launch_variant<NX, kOpQp, kRedDf, float, true>(a, grid, block, smem, st);
-    if (red == kRedF32) return launch_variant<NX, kOpQp, kRedF32, float, true>(a, grid, block, smem, st);
-    if (red == kRedF64) return launch_variant<NX, kOpQp, kRedF64, float, true>(a, grid, block, smem, st);
+    if (f64) return f(PcgVariant<NX, kOpQp, kRedF64, double, true, false>{});
+    if (red == kRedDf) return f(PcgVariant<NX, kOpQp, kRedDf, float, true, false>{});
+    if (red == kRedF32) return f(PcgVariant<NX, kOpQp, kRedF32, float, true, false>{});
+    if (red == kRedF64) return f(PcgVariant<NX, kOpQp, kRedF64, float, true, false>{});
     return cudaErrorInvalidValue;
   }
   if (f64) {
     if (op != kOpQp) return cudaErrorInvalidValue;
-    return launch_variant<NX, kOpQp, kRedF64, double, false>(a, grid, block, smem, st);
+    return f(PcgVariant<NX, kOpQp, kRedF64, double, false, false>{});
   }
 #define SSPCG_PCG_CASE(OPV, REDV) \
-  if (op == OPV && red == REDV) return launch_variant<NX, OPV, REDV, float, false>(a, grid, block, smem, st);
+  if (op == OPV && red == REDV) return f(PcgVariant<NX, OPV, REDV, float, false, false>{});
   SSPCG_PCG_CASE(kOpQp, kRedDf)
   SSPCG_PCG_CASE(kOpQp, kRedF32)
   SSPCG_PCG_CASE(kOpQp, kRedF64)
@@ -645,6 +673,19 @@ cudaError_t launch_pcg_for_nx(int op, int red, bool f64, const PcgArgs &a, int g
   return cudaErrorInvalidValue;
 }
 
+template <int NX>
+cudaError_t launch_pcg_for_nx(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
+                              cudaStream_t st) {
+  return with_pcg_variant<NX>(op, red, f64, a.gscratch != nullptr, a.cg != 0,
+                              [&](auto v) { return decltype(v)::launch(a, grid, block, smem, st); });
+}
+
+template <int NX>
+cudaError_t occupancy_pcg_for_nx(int op, int red, bool f64, bool gv, bool cg, int block, size_t smem, int *ctas) {
+  return with_pcg_variant<NX>(op, red, f64, gv, cg,
+                              [&](auto v) { return decltype(v)::occupancy(block, smem, ctas); });
+}
+
 }  // namespace sspcg
 
 #define SSPCG_INSTANTIATE_PCG(NXV)                                                                           \
@@ -652,5 +693,9 @@ cudaError_t launch_pcg_for_nx(int op, int red, bool f64, const PcgArgs &a, int g
   cudaError_t launch_pcg_nx##NXV(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem, \
                                  cudaStream_t st) {                                                          \
     return launch_pcg_for_nx<NXV>(op, red, f64, a, grid, block, smem, st);                                    \
+  }                                                                                                          \
+  cudaError_t occupancy_pcg_nx##NXV(int op, int red, bool f64, bool gv, bool cg, int block, size_t smem,       \
+                                    int *ctas) {                                                             \
+    return occupancy_pcg_for_nx<NXV>(op, red, f64, gv, cg, block, smem, ctas);                                \
   }                                                                                                          \
   }

@@ -123,6 +123,13 @@ def lib() -> ctypes.CDLL:
             "sspcg_recover_step": [_I32, _I32, _I32] + [_VP] * 10,
             "sspcg_form_gamma_batched": [_VP] * 10,
             "sspcg_recover_step_batched": [_VP] * 11,
+            "sspcg_measure_smem_bandwidth": [_I32, _I32, _VP, _VP],
+            "sspcg_mlp_checkpoint_bytes": [_VP],
+            "sspcg_plan_autotune": [_VP, _I32, _I32] + [_VP] * 14,
+            "sspcg_plan_schedule": [_VP, _I32, _VP, _I32, _VP],
+            "sspcg_autotune_cache_clear": [],
+            "sspcg_mlp_save": [_VP, _VP, ctypes.c_int64, _VP],
+            "sspcg_mlp_load": [_VP, _VP, ctypes.c_int64, _VP],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -298,6 +305,34 @@ def sspcg_plan_capture_pipeline(plan: Plan, kind, A, B, qd, rd, gamma, D, E, PD,
            "sspcg_plan_capture_pipeline")
 
 
+def sspcg_plan_autotune(plan: Plan, kind, A, B, qd, rd, gamma, D, E, PD, PE, lam, iters, relres, status, stream=None,
+                        which="all"):
+    """Tune the plan's PCG launch groups on these inputs: which = "pipeline", "solve" or "all"."""
+    k = PRECOND[kind] if isinstance(kind, str) else int(kind)
+    wh = {"pipeline": 1, "solve": 2, "all": 3}[which]
+    _check(lib().sspcg_plan_autotune(plan.handle, wh, k, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(gamma),
+                                     _ptr(D), _ptr(E), _ptr(PD), _ptr(PE), _ptr(lam), _ptr(iters), _ptr(relres),
+                                     _ptr(status), _stream(stream)), "sspcg_plan_autotune")
+
+
+SCHEDULE_FIELDS = ("nx", "cls", "problems", "max_N", "block", "grid", "smem", "stream", "tuned")
+
+
+def sspcg_plan_schedule(plan: Plan, which: str = "pipeline") -> List[Dict[str, int]]:
+    """Launch groups of a plan: which = "pipeline" (FP32 set), "pipeline_f64" or "solve_qp"."""
+    w = {"pipeline": 0, "pipeline_f64": 1, "solve_qp": 2}[which]
+    cnt = ctypes.c_int32(0)
+    _check(lib().sspcg_plan_schedule(plan.handle, w, None, 0, ctypes.addressof(cnt)), "sspcg_plan_schedule")
+    out = np.zeros((max(cnt.value, 1), len(SCHEDULE_FIELDS)), dtype=np.int32)
+    _check(lib().sspcg_plan_schedule(plan.handle, w, out.ctypes.data, cnt.value, ctypes.addressof(cnt)),
+           "sspcg_plan_schedule")
+    return [dict(zip(SCHEDULE_FIELDS, map(int, row))) for row in out[:cnt.value]]
+
+
+def sspcg_autotune_cache_clear():
+    _check(lib().sspcg_autotune_cache_clear(), "sspcg_autotune_cache_clear")
+
+
 def sspcg_plan_launch(plan: Plan, stream=None):
     _check(lib().sspcg_plan_launch(plan.handle, _stream(stream)), "sspcg_plan_launch")
 
@@ -397,6 +432,14 @@ def sspcg_solve_qp_batched_noalloc(N, nx, nu, A, B, qd, rd, PD, PE, gamma, lam, 
 # ---------------------------------------------------------------------------
 # The QP step around the solve
 # ---------------------------------------------------------------------------
+def sspcg_measure_smem_bandwidth(load_bytes=16, rounds=4096, stream=None) -> float:
+    """Measured shared-memory read bandwidth of the current device in GB/s (a diagnostic)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().sspcg_measure_smem_bandwidth(int(load_bytes), int(rounds), ctypes.addressof(out), _stream(stream)),
+           "sspcg_measure_smem_bandwidth")
+    return out.value
+
+
 def sspcg_form_gamma(N, nx, nu, A, B, qd, rd, c, q, r, gamma, stream=None):
     _check(lib().sspcg_form_gamma(N, nx, nu, _ptr(A), _ptr(B), _ptr(qd), _ptr(rd), _ptr(c), _ptr(q), _ptr(r),
                                   _ptr(gamma), _stream(stream)), "sspcg_form_gamma")
@@ -463,6 +506,24 @@ def sspcg_mlp_get_params(mlp: Mlp, params, stream=None):
 
 def sspcg_mlp_get_grads(mlp: Mlp, grads, stream=None):
     _check(lib().sspcg_mlp_get_grads(mlp.handle, _ptr(grads), _stream(stream)), "sspcg_mlp_get_grads")
+
+
+def sspcg_mlp_checkpoint_bytes() -> int:
+    out = ctypes.c_int64(0)
+    _check(lib().sspcg_mlp_checkpoint_bytes(ctypes.addressof(out)), "sspcg_mlp_checkpoint_bytes")
+    return out.value
+
+
+def sspcg_mlp_save(mlp: Mlp, stream=None) -> np.ndarray:
+    """Checkpoint of the network (parameters, Adam moments and step count, normalisation) as host bytes."""
+    buf = np.zeros(sspcg_mlp_checkpoint_bytes(), dtype=np.uint8)
+    _check(lib().sspcg_mlp_save(mlp.handle, buf.ctypes.data, buf.size, _stream(stream)), "sspcg_mlp_save")
+    return buf
+
+
+def sspcg_mlp_load(mlp: Mlp, buf, stream=None):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().sspcg_mlp_load(mlp.handle, buf.ctypes.data, buf.size, _stream(stream)), "sspcg_mlp_load")
 
 
 def sspcg_mlp_set_normalisation(mlp: Mlp, mu, inv_sigma, stream=None):

@@ -310,3 +310,56 @@ def test_trained_network_reduces_iterations():
     xs, _, _, _, _, _ = block.solve_batch(ev[:32], "sym", 1e-6)
     lams = be.lambdas()
     assert max(rel(lams[i], xs[i]) for i in range(32)) <= LAMBDA_RTOL
+
+
+def test_checkpoint_resumes_training_bit_for_bit():
+    """Train k steps, save, load into a fresh network, train k more: the same parameters, Adam moments, step
+    count and normalisation, bit for bit, as 2k steps without the interruption."""
+    probs = P.make_workload(P.RAGGED_BATCH_4096, count=96)
+    plan, b, net_a = _setup(probs)
+    d = b.dev
+    lam_star = b.lam.clone()
+    init = torch.from_numpy(P.mlp_initial_params(3)).cuda()
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    chunks = [(s0, min(s0 + 16, plan.nprob)) for s0 in range(0, plan.nprob, 16)]
+
+    def steps(net, j0, j1):
+        for j in range(j0, j1):
+            s0, s1 = chunks[(5 * j) % len(chunks)]
+            sspcg.sspcg_mlp_train_step(net, plan, s0, s1, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E,
+                                       b.PD, lam_star, sspcg.adam(lr=1e-3), loss)
+
+    def fresh():
+        net = sspcg.sspcg_mlp_create(4096)
+        sspcg.sspcg_mlp_fit_normalisation(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD)
+        sspcg.sspcg_mlp_set_params(net, init)
+        return net
+
+    k = 7
+    net_a = fresh()
+    steps(net_a, 0, 2 * k)
+    blob_a = sspcg.sspcg_mlp_save(net_a)
+    net_b = fresh()
+    steps(net_b, 0, k)
+    blob_mid = sspcg.sspcg_mlp_save(net_b)
+    del net_b
+    net_c = sspcg.sspcg_mlp_create(4096)  # fresh: zero parameters, identity normalisation, no Adam state
+    sspcg.sspcg_mlp_load(net_c, blob_mid)
+    steps(net_c, k, 2 * k)
+    blob_c = sspcg.sspcg_mlp_save(net_c)
+    assert blob_a.size == sspcg.sspcg_mlp_checkpoint_bytes()
+    assert np.array_equal(blob_a, blob_c)
+    assert not np.array_equal(blob_a, blob_mid)
+    # the resumed network also infers the same lambda0
+    la, lc = plan.empty(sspcg.ARRAY_VEC), plan.empty(sspcg.ARRAY_VEC)
+    sspcg.sspcg_mlp_infer(net_a, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD, la)
+    sspcg.sspcg_mlp_infer(net_c, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD, lc)
+    torch.cuda.synchronize()
+    assert torch.equal(la, lc)
+    # a blob of another layout is refused
+    bad = blob_mid.copy()
+    bad[:8] = np.frombuffer(b"NOTMLPCK", dtype=np.uint8)
+    with pytest.raises(sspcg.SspcgError, match="invalid argument"):
+        sspcg.sspcg_mlp_load(net_c, bad)
+    with pytest.raises(sspcg.SspcgError, match="invalid argument"):
+        sspcg.sspcg_mlp_load(net_c, blob_mid[:100])

@@ -27,19 +27,34 @@ static void fail(const char *what, int op, int N, int nx, int nu, int poly, int 
 }
 static void check_layout(int op, int K, int N, int nx, int nu, int poly, int cg) {
   const PcgLayout L = pcg_layout(op, K, N, nx, nu, poly, cg);
-  const long long offs[] = {L.p, L.r, L.w, L.x, L.e, L.u, L.s, L.v, L.iq, L.ir, L.m0, L.m1, L.pd, L.pe, L.total};
+  const long long offs[] = {L.p, L.r, L.w, L.x, L.e, L.u, L.s, L.v, L.vu, L.iq, L.ir, L.m0, L.m1, L.pd, L.pe, L.total};
   for (long long o : offs)
     if (o % 4 != 0) fail("alignment", op, N, nx, nu, poly, cg, K);
-  for (size_t i = 1; i < sizeof(offs) / sizeof(offs[0]); ++i)
-    if (offs[i] < offs[i - 1]) fail("order", op, N, nx, nu, poly, cg, K);
-  const long long RV = (long long)(N + 1) * vec_stride(nx);
+  // region starts (a vector's region begins one zero segment before its block row 0)
+  const long long g = vec_stride(nx);
+  const long long starts[] = {L.p - g, L.r - g, L.w - g, L.x - g, L.e - g, L.u - g, L.s - g, L.v - g, L.iq, L.ir,
+                              L.m0, L.m1, L.pd, L.pe, L.total};
+  for (size_t i = 1; i < sizeof(starts) / sizeof(starts[0]); ++i)
+    if (starts[i] < starts[i - 1]) fail("order", op, N, nx, nu, poly, cg, K);
+  const long long NXP = vec_stride(nx), RV = (long long)(N + 1) * NXP, RVP = RV + 2 * NXP;
+  // every vector has a zero segment before and after it: regions of (N + 3) segments, block row 0 one in
+  if (L.p != NXP) fail("front segment", op, N, nx, nu, poly, cg, K);
   // the vectors the kernel always uses are distinct and full length
   const long long vec[] = {L.p, L.r, L.w, L.x};
   for (int i = 1; i < 4; ++i)
-    if (vec[i] - vec[i - 1] < RV) fail("vector overlap", op, N, nx, nu, poly, cg, K);
-  if (poly && L.u - L.e < RV) fail("poly vector", op, N, nx, nu, poly, cg, K);
-  if (cg && (L.s - L.u < RV || L.v - L.s < RV)) fail("cg vectors", op, N, nx, nu, poly, cg, K);
-  if (L.v - L.x < RV) fail("x vector", op, N, nx, nu, poly, cg, K);
+    if (vec[i] - vec[i - 1] < RVP) fail("vector overlap", op, N, nx, nu, poly, cg, K);
+  if (poly && L.u - L.e < RVP) fail("poly vector", op, N, nx, nu, poly, cg, K);
+  if (cg && (L.s - L.u < RVP || L.v - L.s < RVP)) fail("cg vectors", op, N, nx, nu, poly, cg, K);
+  if (L.v - L.x < RVP) fail("x vector", op, N, nx, nu, poly, cg, K);
+  if (op == kOpQp) {
+    const long long NUP = vec_stride(nu);
+    // v_x, its back zero segment, v_u's front zero segment, v_u (N rows), then 1/q
+    if (L.vu - L.v != RV + NXP + NUP) fail("v_u offset", op, N, nx, nu, poly, cg, K);
+    if (L.iq - L.vu < (long long)N * NUP) fail("v_u overlap", op, N, nx, nu, poly, cg, K);
+  }
+  // a single knot stages one zero off-diagonal slot
+  if (N == 0 && K > 0 && L.pd + (long long)nx * pad_ld(nx) > L.pe) fail("pd slot", op, N, nx, nu, poly, cg, K);
+  if (N == 0 && K > 0 && L.total - L.pe < (long long)nx * pad_ld(nx)) fail("zero slot", op, N, nx, nu, poly, cg, K);
 }
 int main() {
   const int Ns[] = {0, 1, 2, 3, 7, 16, 31, 64, 100, 128, 255, 512, 1000};

@@ -44,14 +44,19 @@ def test_noalloc_solve_matches_plan_solve_twice():
     assert (ref_st.cpu().numpy() == 0).all()
     shapes = [p.gamma.shape for p in probs]
     ref = plan.unpack(sspcg.ARRAY_VEC, ref_lam, shapes)
+    outs = [(plan.empty(sspcg.ARRAY_VEC, fill=float("nan")),
+             torch.full((plan.nprob,), -7, dtype=torch.int32, device="cuda"),
+             torch.zeros(plan.nprob, dtype=torch.float64, device="cuda"),
+             torch.full((plan.nprob,), 9, dtype=torch.int32, device="cuda")) for _ in range(2)]
+    torch.cuda.synchronize()
     for call in range(2):
-        lam = plan.empty(sspcg.ARRAY_VEC, fill=float("nan"))
-        it = torch.full((plan.nprob,), -7, dtype=torch.int32, device="cuda")
-        rr = torch.zeros(plan.nprob, dtype=torch.float64, device="cuda")
-        st = torch.full((plan.nprob,), 9, dtype=torch.int32, device="cuda")
+        lam, it, rr, st = outs[call]
+        free_before = torch.cuda.mem_get_info()[0]
         sspcg.sspcg_solve_qp_batched_noalloc(Ns, nxs, nus, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE,
                                              d["gamma"], lam, opts, it, rr, st)
         torch.cuda.synchronize()
+        # the call takes no device memory: free bytes are the same after it
+        assert torch.cuda.mem_get_info()[0] == free_before, call
         assert (st.cpu().numpy() == 0).all(), call
         assert np.abs(it.cpu().numpy() - ref_it.cpu().numpy()).max() <= ITER_TOL, call
         got = plan.unpack(sspcg.ARRAY_VEC, lam, shapes)
