@@ -1,14 +1,16 @@
 """Benchmark: batched symmetric-stair PCG solves/s on the ragged 4096-problem workload.
 
-One step = the whole path over one batch, inputs resident in HBM:
-Schur blocks (sspcg_build_schur_batched) -> symmetric stair preconditioner
-(sspcg_build_precond_batched) -> PCG to relative residual 1e-6
-(sspcg_solve_qp_batched).  Prints one JSON line (rank 0).
+One step = the whole path over one batch, inputs resident in HBM: Schur blocks -> symmetric stair
+preconditioner -> PCG to relative residual 1e-6, as one CUDA graph (sspcg_plan_launch of the pipeline
+captured after sspcg_plan_autotune picked every launch group's schedule).  Prints one JSON line (rank 0)
+with the phase rooflines, the end-to-end figure through the host-buffer entry point, the reduction-precision
+and warm-start comparisons, the MPC workload (16,384 problems, 10 re-solves: plain, previous-solution and
+learned warm starts) and the FP64 oracle on the host cores, whose solutions of sampled problems also give
+the lambda error of every GPU result.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-``--impl reference`` times the FP64 CPU oracle (the reference arm) on a
-bounded sample of the same workload on the host cores.
+``--impl reference`` times the FP64 CPU oracle (the reference arm) on the same workload on the host cores.
 """
 from __future__ import annotations
 
@@ -48,16 +50,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+TRAFFIC_FILE = "pcg_kernel_traffic.md"
+
+
 def pcg_traffic():
-    """DRAM bytes of one PCG-only solve of the benchmark batch, from the committed ncu launch-list summary,
-    if the kernel source is unchanged since it was captured (kernel_source_hash); else None."""
+    """DRAM bytes per PCG launch set of the benchmark batch, from the committed ncu summary
+    (profiles/pcg_kernel_traffic.md), if the kernel source is unchanged since it was captured
+    (kernel_source_hash); else None."""
     try:
-        text = open(os.path.join(ROOT, "profiles", "launches_ragged4096_pipeline.md")).read()
+        text = open(os.path.join(ROOT, "profiles", TRAFFIC_FILE)).read()
         vals = dict(line.split(":", 1) for line in text.splitlines()
-                    if line.startswith(("pcg_traffic_bytes_per_solve:", "source_sha256_16:")))
+                    if line.startswith(("pcg_traffic_bytes_per_launch:", "source_sha256_16:")))
         if kernel_source_hash() != vals["source_sha256_16"].strip():
             return None
-        return int(vals["pcg_traffic_bytes_per_solve"])
+        return int(vals["pcg_traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -72,6 +78,18 @@ def _hbm_peak():
 
 
 HBM_PEAK_GBS, HBM_PEAK_SOURCE = _hbm_peak()
+
+
+def _bf16_peak():
+    """Measured dense bf16 burst throughput (TFLOP/s) from MEASURED_PEAKS.json, else 1900 (fallback)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
+BF16_PEAK_TFLOPS = _bf16_peak()
 MLP_MAX_ROWS = 1 << 19  # network workspace: the whole warm-start batch (266,240 knot rows) in one chunk
 
 
@@ -81,21 +99,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sspcg", choices=["sspcg", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target duration of the CPU baseline sample")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target duration of each CPU baseline timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--problems", type=int, default=0,
                     help="first N problems of the workload only (small profiler captures); 0: all")
-    ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm start (and its MPC arm)")
     ap.add_argument("--no-poly", action="store_true", help="skip the polynomial-preconditioner comparison")
     ap.add_argument("--no-full", action="store_true", help="skip the full-cost-block comparison")
     ap.add_argument("--no-paper-stats", action="store_true",
                     help="skip the Fig. 1-3 statistics (spectra and iterations per preconditioner)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer timing")
     ap.add_argument("--train-problems", type=int, default=4096, help="training problems of the warm-start network")
     ap.add_argument("--train-epochs", type=int, default=1)
     ap.add_argument("--train-gammas", type=int, default=49,
                     help="right-hand sides per training problem (its own gamma and seeded N(0, 1) draws)")
-    ap.add_argument("--mpc", action="store_true",
-                    help="add the MPC batch (16384 problems, 10 sequential re-solves, plain vs warm-started)")
+    ap.add_argument("--no-mpc", action="store_true", help="skip the MPC workload (16384 problems, 10 re-solves)")
     ap.add_argument("--mpc-resolves", type=int, default=10)
     ap.add_argument("--mpc-problems", type=int, default=0, help="first N problems of the MPC batch; 0: all")
     return ap.parse_args()
@@ -194,27 +212,45 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
-def cpu_baseline(probs, target_s: float, tol: float):
-    """The FP64 oracle (build + preconditioner + PCG per problem, OpenMP over problems) on the first
-    problems of the workload, growing the sample until it runs about ``target_s`` seconds; when the whole
-    workload takes less, it is solved in repeated passes (at most 50) for about ``target_s`` seconds."""
+def cpu_baseline(probs, target_s: float, tol: float, samples=None):
+    """The FP64 oracle (Schur build, preconditioner and PCG per problem, OpenMP over problems) on the host
+    cores, built with gcc -O3: a sample of the first problems of the workload, sized so that one pass on all
+    cores takes about target_s / 10, timed five times on all cores and five times on one core (a sample a
+    core count smaller), median of each.  The oracle also solves ``samples`` (name -> list of problems); their
+    solutions, returned beside the timing, give the lambda error of the GPU results on the same problems."""
     from oracle import block
+    block.build()
     cores = os.cpu_count() or 1
+    run = lambda sub, nt: block.solve_batch(sub, PRECOND, tol, nthreads=nt)
     m = min(64, len(probs))
     while True:
-        _, iters, _, status, used, dt = block.solve_batch(probs[:m], PRECOND, tol, nthreads=cores)
-        if dt >= target_s or m >= len(probs):
+        _, _, _, _, used, dt = run(probs[:m], cores)
+        if dt >= target_s / 10 or m >= len(probs):
             break
-        m = min(len(probs), max(m + 1, int(m * min(8.0, 1.2 * target_s / max(dt, 1e-3)))))
-    passes = 1
-    if dt < target_s:
-        passes = min(50, max(2, int(np.ceil(target_s / max(dt, 1e-3)))))
-        dt = 0.0
-        for _ in range(passes):
-            dt += block.solve_batch(probs[:m], PRECOND, tol, nthreads=cores)[5]
-    what = f"first {m} of the {len(probs)} problems" + (f", {passes} passes" if passes > 1 else "")
-    return {"value": passes * m / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
-            "sample": what + " (FP64 Schur build, preconditioner and PCG)", "seconds": dt}
+        m = min(len(probs), max(m + 1, int(m * min(8.0, 1.2 * (target_s / 10) / max(dt, 1e-3)))))
+    t_all = statistics.median(run(probs[:m], cores)[5] for _ in range(5))
+    m1 = max(4, m // max(1, used))
+    t_one = statistics.median(run(probs[:m1], 1)[5] for _ in range(5))
+    refs = {}
+    for name, sub in (samples or {}).items():
+        refs[name] = run(sub, cores)[0]
+    base = {"value": m / t_all, "unit": UNIT, "cores": int(used), "kind": "oracle",
+            "sample": f"first {m} of the {len(probs)} problems per pass, median of 5 passes on {used} cores "
+                      f"(FP64 Schur build, preconditioner and PCG; gcc -O3)",
+            "seconds_per_pass": t_all,
+            "one_core": {"value": m1 / t_one, "unit": UNIT, "cores": 1,
+                         "sample": f"first {m1} problems per pass, median of 5 passes", "seconds_per_pass": t_one}}
+    return base, refs
+
+
+def lambda_error(got, ref) -> float:
+    """Largest relative 2-norm error of GPU solutions against the oracle's over a sample."""
+    worst = 0.0
+    for g, r in zip(got, ref):
+        r = np.asarray(r, dtype=np.float64).ravel()
+        nr = np.linalg.norm(r)
+        worst = max(worst, float(np.linalg.norm(np.asarray(g, dtype=np.float64).ravel() - r) / (nr if nr else 1.0)))
+    return worst
 
 
 def run_reference(args, world, rank):
@@ -290,19 +326,33 @@ def train_warm_start(args, torch, sspcg, rank):
     return net, hist, len(train) * len(gammas)
 
 
-def warm_start_comparison(args, torch, sspcg, stream, rank):
-    """Held-out warm-start workload (4096 problems, nx = 14, N = 64, h = 0.01): the whole path from lambda0 = 0
-    against the whole path started from the trained network (inference inside the timed step), same GPU."""
-    t0 = time.time()
-    net, hist, ntrain = train_warm_start(args, torch, sspcg, rank)
+def timed_steps(torch, stream, fn, steps, warmup):
+    """Mean ms of ``steps`` calls of fn on ``stream`` after ``warmup`` untimed ones (CUDA events)."""
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
     torch.cuda.synchronize()
-    train_s = time.time() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def warm_start_comparison(args, torch, sspcg, stream, rank, net, sample=64):
+    """Held-out warm-start workload (4096 problems, nx = 14, N = 64, h = 0.01): the whole path from lambda0 = 0
+    against the whole path started from the trained network (inference inside the timed step), same GPU.
+    Returns the results and the sampled problems with each arm's lambda."""
     w = P.WARMSTART_EVAL_4096
     probs = P.make_workload(w, count=w.nprob, start=rank_start(rank, w.nprob))
     plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
                                    sspcg.options(tol=w.tol))
     b = sspcg.Batch(plan, probs)
     d = b.dev
+    sspcg.sspcg_plan_autotune(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD, b.PE,
+                              b.lam, b.iters, b.relres, b.status, stream, which="pipeline")
 
     def plain():
         sspcg.sspcg_pipeline_batched(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD,
@@ -312,23 +362,14 @@ def warm_start_comparison(args, torch, sspcg, stream, rank):
         sspcg.sspcg_pipeline_warm_batched(plan, net, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E,
                                           b.PD, b.PE, b.lam, b.iters, b.relres, b.status, stream)
 
-    out = {}
+    out, lams = {}, {}
     for name, fn in (("plain", plain), ("warm", warm)):
-        with torch.cuda.stream(stream):
-            for _ in range(max(3, args.warmup)):
-                fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = timed_steps(torch, stream, fn, args.steps, max(3, args.warmup))
         it = b.iters.cpu().numpy()
         ok = bool((b.status.cpu().numpy() == 0).all() and (b.relres.cpu().numpy() <= w.tol).all())
         out[name] = {"solves_per_s": len(probs) / (ms / 1e3), "ms_per_step": ms, "iters_mean": float(it.mean()),
                      "iters_p50": float(np.percentile(it, 50)), "all_converged": ok}
+        lams[name] = b.lambdas()[:sample]
     # inference alone (features + three products + scatter), each product engine
     b.pipeline(PRECOND, stream)
     lam0 = plan.empty(sspcg.ARRAY_VEC)
@@ -336,29 +377,19 @@ def warm_start_comparison(args, torch, sspcg, stream, rank):
     infer = {}
     for engine in ("tcgen05", "mma_sync"):
         sspcg.sspcg_mlp_set_engine(net, engine)
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                sspcg.sspcg_mlp_infer(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD, lam0, stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            sspcg.sspcg_mlp_infer(net, plan, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.PD, lam0, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        infer[engine] = {"ms": ms, "tflops": rows * MLP_FLOP_PER_ROW / (ms / 1e3) / 1e12}
+        ms = timed_steps(torch, stream, lambda: sspcg.sspcg_mlp_infer(net, plan, d["A"], d["B"], d["qd"], d["rd"],
+                                                                       d["gamma"], b.PD, lam0, stream),
+                         args.steps, 3)
+        infer[engine] = {"ms": ms, "tflops": rows * MLP_FLOP_PER_ROW / (ms / 1e3) / 1e12,
+                         "frac_of_bf16_peak": rows * MLP_FLOP_PER_ROW / (ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS}
     sspcg.sspcg_mlp_set_engine(net, "tcgen05")
     stats = sspcg.plan_stats(plan)
-    # warm steps add, per chunk of MLP_MAX_ROWS rows, features, three products and the scatter
-    chunks = -(-sum(p.n for p in probs) // MLP_MAX_ROWS)
-    return {"workload": w.name, "train_problems": args.train_problems, "train_solves": ntrain,
-            "train_epochs": args.train_epochs,
-            "train_loss": [round(x, 4) for x in hist], "train_seconds": round(train_s, 2),
-            "plain": out["plain"], "warm": out["warm"],
-            "inference": {"rows": rows, "flop_per_row": MLP_FLOP_PER_ROW, **infer},
-            "speedup": out["warm"]["solves_per_s"] / out["plain"]["solves_per_s"],
-            "gpu_launches": args.steps * (2 * step_launches(probs, stats) + 5 * chunks)}
+    chunks = -(-rows // MLP_MAX_ROWS)
+    return ({"workload": w.name, "plain": out["plain"], "warm": out["warm"],
+             "inference": {"rows": rows, "flop_per_row": MLP_FLOP_PER_ROW, "peak_tflops": BF16_PEAK_TFLOPS, **infer},
+             "speedup": out["warm"]["solves_per_s"] / out["plain"]["solves_per_s"],
+             "gpu_launches": args.steps * (2 * step_launches(probs, stats) + 5 * chunks)},
+            probs[:sample], lams)
 
 
 def step_launches(probs, stats):
@@ -527,12 +558,14 @@ def full_cost_comparison(args, torch, sspcg, stream, probs, w):
     return out
 
 
-def mpc_comparison(args, torch, sspcg, stream, rank):
-    """MPC batch: 16384 problems (N ~ U{64..512}, nx ~ U{4..28}) whose gamma is perturbed by 1 % for each of
+def mpc_comparison(args, torch, sspcg, stream, rank, net=None, sample=32):
+    """MPC workload: 16384 problems (N ~ U{64..512}, nx ~ U{4..28}) whose gamma is perturbed by 1 % for each of
     ``--mpc-resolves`` sequential re-solves.  Blocks and preconditioner are built once (A, B, Q, R do not
-    change); each re-solve is one PCG launch set, from lambda0 = 0 (plain) or from the previous solution
-    (warm, with fallback).  These problems do not fit in shared memory: the PCG streams its blocks from
-    HBM, so the roofline is the measured HBM copy bandwidth."""
+    change); each re-solve is one PCG launch set (autotuned) from lambda0 = 0 (plain), from the previous
+    solution (previous), or from the learned network's lambda0 = MLP(features with the new gamma), inference
+    inside the timed re-solve (mlp); warm starts use the fallback to zero.  Most of these problems do not fit
+    in shared memory: their blocks stream from L2/HBM, so the roofline is the measured HBM copy bandwidth.
+    Returns the results and, per arm, the final re-solve's lambda of ``sample`` spread problems."""
     import dataclasses
     w = P.MPC_BATCH_16384
     t0 = time.time()
@@ -544,9 +577,13 @@ def mpc_comparison(args, torch, sspcg, stream, rank):
     b = sspcg.Batch(plan, probs)
     d = b.dev
     R = args.mpc_resolves
-    # gamma of re-solve 0 warms up (and starts the warm chain); re-solves 1..R are timed
+    # gamma of re-solve 0 warms up (and starts the previous-solution chain); re-solves 1..R are timed
     gammas = [torch.from_numpy(plan.pack(sspcg.ARRAY_VEC, [P.perturb_gamma(p, r) for p in probs])).cuda()
               for r in range(R + 1)]
+    t0 = time.time()
+    sspcg.sspcg_plan_autotune(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], gammas[0], b.D, b.E, b.PD, b.PE,
+                              b.lam, b.iters, b.relres, b.status, stream, which="solve")
+    tune_s = time.time() - t0
     with torch.cuda.stream(stream):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -555,16 +592,22 @@ def mpc_comparison(args, torch, sspcg, stream, rank):
         e1.record(stream)
     torch.cuda.synchronize()
     build_ms = e0.elapsed_time(e1)
+    idx = np.linspace(0, len(probs) - 1, sample).astype(int)
 
     def solve(g):
         sspcg.sspcg_solve_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE, g, b.lam, b.iters, b.relres,
                                      b.status, stream)
 
-    out = {}
-    for mode in ("plain", "warm"):
+    def infer(g):
+        sspcg.sspcg_mlp_infer(net, plan, d["A"], d["B"], d["qd"], d["rd"], g, b.PD, b.lam, stream)
+
+    out, lams = {}, {}
+    for mode in ("plain", "previous", "mlp"):
+        if mode == "mlp" and net is None:
+            continue
         b.lam.zero_()
         with torch.cuda.stream(stream):
-            solve(gammas[0])  # warm-up (also the start of the warm chain)
+            solve(gammas[0])  # warm-up (also the start of the previous-solution chain)
         torch.cuda.synchronize()
         iters, ok, alg = [], True, 0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -574,6 +617,8 @@ def mpc_comparison(args, torch, sspcg, stream, rank):
                 b.lam.zero_()
             torch.cuda.synchronize()
             e0.record(stream)
+            if mode == "mlp":
+                infer(gammas[r])
             solve(gammas[r])
             e1.record(stream)
             torch.cuda.synchronize()
@@ -586,12 +631,30 @@ def mpc_comparison(args, torch, sspcg, stream, rank):
         out[mode] = {"solves_per_s": len(probs) * R / (ms / 1e3), "ms_per_resolve": ms / R,
                      "iters_mean_per_resolve": [round(x, 2) for x in iters], "all_converged": ok,
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                                  "frac": gbs / HBM_PEAK_GBS, "peak_source": HBM_PEAK_SOURCE}}
+                                  "frac": gbs / HBM_PEAK_GBS, "peak_source": HBM_PEAK_SOURCE,
+                                  "note": "algorithmic bytes over the re-solve time: every block read counted as "
+                                          "if it came from HBM (an upper bound on the HBM rate)"}}
+        allx = b.lambdas()
+        lams[mode] = [allx[i] for i in idx]
     stats = sspcg.plan_stats(plan)
-    return {"workload": w.name, "problems": len(probs), "resolves": R, "generate_seconds": round(gen_s, 1),
-            "build_ms": build_ms, "plain": out["plain"], "warm": out["warm"],
-            "speedup": out["warm"]["solves_per_s"] / out["plain"]["solves_per_s"],
-            "streamed_problems": stats["solve_qp_stream"], "pcg_launches_per_resolve": stats["solve_qp_launches"]}
+    last = [dataclasses.replace(probs[i], gamma=P.perturb_gamma(probs[i], R)) for i in idx]
+    res = {"workload": w.name, "problems": len(probs), "resolves": R, "generate_seconds": round(gen_s, 1),
+           "tune_seconds": round(tune_s, 2), "build_ms": build_ms, **out,
+           "speedup_previous": out["previous"]["solves_per_s"] / out["plain"]["solves_per_s"],
+           "streamed_problems": stats["solve_qp_stream"], "pcg_launches_per_resolve": stats["solve_qp_launches"]}
+    if "mlp" in out:
+        res["speedup_mlp"] = out["mlp"]["solves_per_s"] / out["plain"]["solves_per_s"]
+    return res, last, lams
+
+
+def build_bytes(probs) -> int:
+    """HBM bytes the two build calls must move at least: read A, B, diag Q, diag R once, write the Schur blocks
+    D, E and the preconditioner blocks PD, PE once (FP32)."""
+    tot = 0
+    for p in probs:
+        n, N, m, u = p.N + 1, p.N, p.nx, p.nu
+        tot += N * m * m + N * m * u + n * m + N * u + 2 * (n * m * m + N * m * m)
+    return 4 * tot
 
 
 def main():
@@ -613,17 +676,32 @@ def main():
     nprob = args.problems if args.problems > 0 else w.nprob
     probs = P.make_workload(w, count=nprob, start=rank_start(rank, nprob))  # weak scaling
     opts = sspcg.options(tol=w.tol)
+    stream = torch.cuda.Stream()
+    warm = max(3, args.warmup)
+    smem_4 = sspcg.sspcg_measure_smem_bandwidth(4, 8192)
+    smem_16 = sspcg.sspcg_measure_smem_bandwidth(16, 8192)
+    smem_peak = max(smem_4, smem_16)
+
+    # the schedule the library picks without tuning (timed for comparison), then the autotuned plan whose
+    # pipeline, captured in one CUDA graph, is the timed step
+    plan_h = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs], opts)
+    bh = sspcg.Batch(plan_h, probs)
+    heuristic_ms = timed_steps(torch, stream, lambda: bh.pipeline(PRECOND, stream), args.steps, warm)
+    del bh, plan_h
     plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs], opts)
     b = sspcg.Batch(plan, probs, pin=True)
     d = b.dev
-    stream = torch.cuda.Stream()
+    t0 = time.time()
+    sspcg.sspcg_plan_autotune(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD, b.PE,
+                              b.lam, b.iters, b.relres, b.status, stream)
+    tune_s = time.time() - t0
+    b.capture(PRECOND, stream)
 
     def step():
-        sspcg.sspcg_pipeline_batched(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD,
-                                     b.PE, b.lam, b.iters, b.relres, b.status, stream)
+        sspcg.sspcg_plan_launch(plan, stream)
 
     with torch.cuda.stream(stream):
-        for _ in range(max(3, args.warmup)):
+        for _ in range(warm):
             step()
     torch.cuda.synchronize()
     if world > 1:
@@ -645,6 +723,9 @@ def main():
     relres = b.relres.cpu().numpy()
     ok = bool((status == 0).all() and (relres <= w.tol).all())
     value = job_throughput(world, nprob, args.steps, total_ms)
+    sample3 = list(range(min(256, nprob)))
+    lam_main = b.lambdas()
+    lam_main = [lam_main[i] for i in sample3]
 
     # The phases timed apart: the PCG launches alone (FP32, every problem, all groups concurrently) on the
     # blocks the pipeline built, and the two build calls alone.
@@ -659,108 +740,169 @@ def main():
         sspcg.sspcg_build_schur_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.D, b.E, stream)
         sspcg.sspcg_build_precond_batched(plan, PRECOND, b.D, b.E, b.PD, b.PE, st_d, stream)
 
-    def timed(fn):
-        with torch.cuda.stream(stream):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps
-
-    build_ms = timed(build_only)
-    pcg_ms = timed(pcg_only)
-    # roofline of the dominant kernel (the PCG launches): algorithmic bytes per launch / launch time
+    build_ms = timed_steps(torch, stream, build_only, args.steps, 1)
+    pcg_ms = timed_steps(torch, stream, pcg_only, args.steps, 1)
+    # roofline of the dominant kernel (the PCG launches): algorithmic bytes per launch set / its time
     iters_pcg = it_d.cpu().numpy().astype(np.int64)
     alg_bytes = sum(int(iters_pcg[i]) * algorithmic_bytes_per_iteration(p) for i, p in enumerate(probs))
     achieved_gbs = alg_bytes / (pcg_ms / 1e3) / 1e9
-    props = torch.cuda.get_device_properties(local)
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    smem_peak_gbs = props.multi_processor_count * SMEM_BYTES_PER_CLK_PER_SM * sm_max * 1e6 / 1e9
+    bb = build_bytes(probs)
+    build_gbs = bb / (build_ms / 1e3) / 1e9
 
-    # end to end through the host-buffer C-ABI call (copies inside the timed region): the asynchronous
-    # entry point overlaps one step's host-to-device copy with the previous step's compute; the
-    # synchronous one (copy in, compute, copy out, wait) is timed beside it
-    h = b.host
-    lam_h = torch.zeros(max(int(plan.sizes[sspcg.ARRAY_VEC]), 4)).pin_memory()
-    it_h = torch.zeros(plan.nprob, dtype=torch.int32).pin_memory()
-    rr_h = torch.zeros(plan.nprob, dtype=torch.float64).pin_memory()
-    st_h = torch.zeros(plan.nprob, dtype=torch.int32).pin_memory()
-    host_args = (plan, PRECOND, h["A"], h["B"], h["qd"], h["rd"], h["gamma"], lam_h, it_h, rr_h, st_h, stream)
+    h2d = d2h = 0
+    e2e_ms = e2e_sync_ms = None
+    e2e_ok = None
+    if not args.no_e2e:
+        # end to end through the host-buffer C-ABI call (copies inside the timed region): the asynchronous
+        # entry point overlaps one step's host-to-device copy with the previous step's compute; the
+        # synchronous one (copy in, compute, copy out, wait) is timed beside it
+        h = b.host
+        lam_h = torch.zeros(max(int(plan.sizes[sspcg.ARRAY_VEC]), 4)).pin_memory()
+        it_h = torch.zeros(plan.nprob, dtype=torch.int32).pin_memory()
+        rr_h = torch.zeros(plan.nprob, dtype=torch.float64).pin_memory()
+        st_h = torch.zeros(plan.nprob, dtype=torch.int32).pin_memory()
+        host_args = (plan, PRECOND, h["A"], h["B"], h["qd"], h["rd"], h["gamma"], lam_h, it_h, rr_h, st_h, stream)
 
-    def e2e_timed(call, join):
-        with torch.cuda.stream(stream):
-            for _ in range(max(3, args.warmup)):
-                call(*host_args)
-            join()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                call(*host_args)
-            join()
-            e1.record(stream)
-            torch.cuda.synchronize()
-        return max_over_ranks(e0.elapsed_time(e1), world)
+        def e2e_timed(call, join):
+            with torch.cuda.stream(stream):
+                for _ in range(warm):
+                    call(*host_args)
+                join()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    call(*host_args)
+                join()
+                e1.record(stream)
+                torch.cuda.synchronize()
+            return max_over_ranks(e0.elapsed_time(e1), world)
 
-    e2e_sync_ms = e2e_timed(sspcg.sspcg_pipeline_host, lambda: None)
-    e2e_ms = e2e_timed(sspcg.sspcg_pipeline_host_async, lambda: sspcg.sspcg_plan_join(plan, stream))
-    e2e_ok = bool((st_h.numpy() == 0).all()) and torch.equal(lam_h, b.lam.cpu())
-    h2d = sum(int(h[k].numel()) * 4 for k in ("A", "B", "qd", "rd", "gamma"))
-    d2h = int(lam_h.numel()) * 4 + plan.nprob * (4 + 4 + 8)
+        e2e_sync_ms = e2e_timed(sspcg.sspcg_pipeline_host, lambda: None)
+        e2e_ms = e2e_timed(sspcg.sspcg_pipeline_host_async, lambda: sspcg.sspcg_plan_join(plan, stream))
+        e2e_ok = bool((st_h.numpy() == 0).all()) and torch.equal(lam_h, b.lam.cpu())
+        h2d = sum(int(h[k].numel()) * 4 for k in ("A", "B", "qd", "rd", "gamma"))
+        d2h = int(lam_h.numel()) * 4 + plan.nprob * (4 + 4 + 8)
 
     if rank != 0:
         if world > 1:
             dist.barrier()
         return
     stats = sspcg.plan_stats(plan)
+    sched = sspcg.sspcg_plan_schedule(plan, "pipeline") + sspcg.sspcg_plan_schedule(plan, "pipeline_f64")
+    traffic = pcg_traffic() if nprob == w.nprob else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(w, nprob),
         "iters": {"mean": float(iters.mean()), "min": int(iters.min()), "max": int(iters.max()),
                   "p50": float(np.percentile(iters, 50)), "p90": float(np.percentile(iters, 90))},
         "all_converged": ok,
         "pcg_ms_per_step": pcg_ms,
-        "roofline": {"bound": "smem", "achieved": achieved_gbs, "peak": smem_peak_gbs, "unit": "GB/s",
-                     "frac": achieved_gbs / smem_peak_gbs,
-                     "traffic": pcg_traffic() if nprob == w.nprob else None,
-                     "traffic_note": "DRAM bytes per PCG-only solve of the batch (ncu, profiles/); the blocks are "
+        "roofline": {"bound": "smem", "achieved": achieved_gbs, "peak": smem_peak, "unit": "GB/s",
+                     "frac": achieved_gbs / smem_peak, "traffic": traffic,
+                     "traffic_note": "DRAM bytes per PCG launch set of the batch (ncu, profiles/); the blocks are "
                                      "read from shared memory and L2, so HBM traffic is far below the "
                                      "algorithmic bytes",
                      "kernel": "pcg_kernel (all FP32 PCG launches of the batch, timed alone)",
-                     "peak_source": f"derived: {props.multi_processor_count} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk "
-                                    f"x {sm_max:.0f} MHz"},
-        "e2e": {"value": job_throughput(world, nprob, args.steps, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "entry": "sspcg_pipeline_host_async (two device slots, copies "
-                                                     "overlapped with the previous step's compute)",
-                "results_match_device_path": e2e_ok,
-                "synchronous": job_throughput(world, nprob, args.steps, e2e_sync_ms)},
-        "gpu_launches": None,
+                     "peak_source": "measured: sspcg_measure_smem_bandwidth, conflict-free shared-memory reads "
+                                    "on every SM (the better of 32-bit and 128-bit loads)",
+                     "peak_measured_lds32_gbs": smem_4, "peak_measured_lds128_gbs": smem_16,
+                     "frac_of_derived_peak": achieved_gbs / (torch.cuda.get_device_properties(local)
+                                                             .multi_processor_count * SMEM_BYTES_PER_CLK_PER_SM *
+                                                             (clk.get("sm_max_mhz") or 2070.0) * 1e-3)},
+        "build": {"ms_per_step": build_ms, "roofline": {"bound": "hbm", "achieved": build_gbs, "peak": HBM_PEAK_GBS,
+                                                        "unit": "GB/s", "frac": build_gbs / HBM_PEAK_GBS,
+                                                        "bytes": bb, "peak_source": HBM_PEAK_SOURCE}},
+        "gpu_launches": args.steps * step_launches(probs, stats),
         "clocks": clk,
     }
-    line["gpu_launches"] = args.steps * step_launches(probs, stats)
-    line["schedules"] = {"resident_fp32_problems": stats["pipeline_resident"],
-                         "streamed_fp32_problems": stats["pipeline_stream"],
-                         "fp64_problems": stats["pipeline_f64"],
-                         "pcg_launches_per_step": stats["pipeline_launches"]}
-    line["build_ms_per_step"] = build_ms
+    if e2e_ms is not None:
+        line["e2e"] = {"value": job_throughput(world, nprob, args.steps, e2e_ms), "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "entry": "sspcg_pipeline_host_async (two device slots, copies overlapped with the previous "
+                                "step's compute)", "results_match_device_path": e2e_ok,
+                       "synchronous": job_throughput(world, nprob, args.steps, e2e_sync_ms)}
+    line["schedules"] = {"autotune_seconds": round(tune_s, 2), "step": "one CUDA graph (sspcg_plan_launch)",
+                         "heuristic_ms_per_step": heuristic_ms, "tuned_ms_per_step": total_ms / args.steps,
+                         "resident_fp32_problems": stats["pipeline_resident"],
+                         "streamed_fp32_problems": stats["pipeline_stream"], "fp64_problems": stats["pipeline_f64"],
+                         "pcg_launches_per_step": stats["pipeline_launches"],
+                         "groups": [{k: g[k] for k in ("nx", "cls", "problems", "max_N", "block", "grid", "stream")}
+                                    for g in sched]}
+
+    # the FP64 reduction mode beside the double-float default
+    plan_r = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
+                                     sspcg.options(tol=w.tol, reduction="f64"))
+    br = sspcg.Batch(plan_r, probs)
+    dr = br.dev
+    sspcg.sspcg_plan_autotune(plan_r, PRECOND, dr["A"], dr["B"], dr["qd"], dr["rd"], dr["gamma"], br.D, br.E, br.PD,
+                              br.PE, br.lam, br.iters, br.relres, br.status, stream, which="pipeline")
+    ms_r = timed_steps(torch, stream, lambda: br.pipeline(PRECOND, stream), args.steps, warm)
+    lam_r = br.lambdas()
+    line["reduction_f64"] = {"solves_per_s": nprob / (ms_r / 1e3), "ms_per_step": ms_r,
+                             "iters_mean": float(br.iters.cpu().numpy().mean()),
+                             "all_converged": bool((br.status.cpu().numpy() == 0).all()),
+                             "note": "alpha/beta dot products in native FP64 instead of double-float"}
+    lam_r = [lam_r[i] for i in sample3]
+    del br, plan_r
+
     if not args.no_poly:
         line["polynomial_preconditioners"] = poly_comparison(args, torch, sspcg, stream, probs, w)
     if not args.no_full:
         line["full_cost_blocks"] = full_cost_comparison(args, torch, sspcg, stream, probs, w)
     if not args.no_paper_stats:
         line["paper_statistics"] = paper_statistics(torch, sspcg)
+    net = None
+    samples = {"ragged": [probs[i] for i in sample3]}
+    gpu_lams = {"value": ("ragged", lam_main), "reduction_f64": ("ragged", lam_r)}
     if not args.no_warm_start:
-        line["warm_start"] = warm_start_comparison(args, torch, sspcg, stream, rank)
-    if args.mpc:
-        line["mpc"] = mpc_comparison(args, torch, sspcg, stream, rank)
+        t0 = time.time()
+        net, hist, ntrain = train_warm_start(args, torch, sspcg, rank)
+        torch.cuda.synchronize()
+        train_s = time.time() - t0
+        ws, ws_probs, ws_lams = warm_start_comparison(args, torch, sspcg, stream, rank, net)
+        ws.update({"train_problems": args.train_problems, "train_solves": ntrain, "train_epochs": args.train_epochs,
+                   "train_loss": [round(x, 4) for x in hist], "train_seconds": round(train_s, 2)})
+        line["warm_start"] = ws
+        samples["warmstart_eval"] = ws_probs
+        gpu_lams["warm_start.plain"] = ("warmstart_eval", ws_lams["plain"])
+        gpu_lams["warm_start.warm"] = ("warmstart_eval", ws_lams["warm"])
+
+        # warm start vs plain on the benchmark workload itself (direct launches of both pipelines)
+        def plain3():
+            sspcg.sspcg_pipeline_batched(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD,
+                                         b.PE, b.lam, b.iters, b.relres, b.status, stream)
+
+        def warm3():
+            sspcg.sspcg_pipeline_warm_batched(plan, net, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D,
+                                              b.E, b.PD, b.PE, b.lam, b.iters, b.relres, b.status, stream)
+
+        r3 = {}
+        for name, fn in (("plain", plain3), ("warm", warm3)):
+            ms = timed_steps(torch, stream, fn, args.steps, warm)
+            r3[name] = {"solves_per_s": nprob / (ms / 1e3), "ms_per_step": ms,
+                        "iters_mean": float(b.iters.cpu().numpy().mean()),
+                        "all_converged": bool((b.status.cpu().numpy() == 0).all())}
+            lw = b.lambdas()
+            gpu_lams[f"warm_start_ragged.{name}"] = ("ragged", [lw[i] for i in sample3])
+        r3["speedup"] = r3["warm"]["solves_per_s"] / r3["plain"]["solves_per_s"]
+        line["warm_start_ragged"] = r3
+    if not args.no_mpc:
+        mpc, mpc_probs, mpc_lams = mpc_comparison(args, torch, sspcg, stream, rank, net)
+        line["mpc"] = mpc
+        samples["mpc_last_resolve"] = mpc_probs
+        for k, v in mpc_lams.items():
+            gpu_lams[f"mpc.{k}"] = ("mpc_last_resolve", v)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(probs, args.cpu_seconds, w.tol)
+        base, refs = cpu_baseline(probs, args.cpu_seconds, w.tol, samples)
+        line["cpu_baseline"] = base
+        line["lambda_error"] = {
+            name: {"max_rel": lambda_error(lams, refs[smp]), "problems": len(lams), "sample": smp}
+            for name, (smp, lams) in gpu_lams.items()}
+        line["lambda_error"]["note"] = ("max over the sampled problems of ||lambda - lambda_oracle|| / "
+                                        "||lambda_oracle||; the oracle solves from zero in FP64 to the same tolerance")
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

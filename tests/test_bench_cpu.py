@@ -22,22 +22,21 @@ def test_step_launches_count():
 
 
 def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
-    assert isinstance(bench.pcg_traffic(), int)
-    # a copy of the tree whose kernel source differs: the recorded figure no longer applies
+    """The recorded DRAM figure is reported only while the kernel source hashes to the value recorded with it."""
     root = tmp_path / "repo"
     (root / "profiles").mkdir(parents=True)
     (root / "paper_2309_06427_gb300" / "csrc").mkdir(parents=True)
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "launches_ragged4096_pipeline.md"), root / "profiles")
     for f in ("pcg.cuh", "kernels.h"):
         shutil.copy(os.path.join(bench.ROOT, "paper_2309_06427_gb300", "csrc", f),
                     root / "paper_2309_06427_gb300" / "csrc" / f)
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.pcg_traffic() == int(open(os.path.join(root, "profiles", "launches_ragged4096_pipeline.md"))
-                                      .read().split("pcg_traffic_bytes_per_solve:")[1].split()[0])
+    with open(root / "profiles" / bench.TRAFFIC_FILE, "w") as f:
+        f.write(f"pcg_traffic_bytes_per_launch: 123456\nsource_sha256_16: {bench.kernel_source_hash()}\n")
+    assert bench.pcg_traffic() == 123456
     # a comment does not change the kernel; code does
     with open(root / "paper_2309_06427_gb300" / "csrc" / "pcg.cuh", "a") as f:
         f.write("\n// a comment\n")
-    assert bench.pcg_traffic() is not None
+    assert bench.pcg_traffic() == 123456
     with open(root / "paper_2309_06427_gb300" / "csrc" / "pcg.cuh", "a") as f:
         f.write("\nnamespace sspcg { constexpr int kChanged = 1; }\n")
     assert bench.pcg_traffic() is None
