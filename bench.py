@@ -116,6 +116,9 @@ def parse():
     ap.add_argument("--no-mpc", action="store_true", help="skip the MPC workload (16384 problems, 10 re-solves)")
     ap.add_argument("--mpc-resolves", type=int, default=10)
     ap.add_argument("--mpc-problems", type=int, default=0, help="first N problems of the MPC batch; 0: all")
+    ap.add_argument("--profile", choices=["step", "pcg", "build"], default=None,
+                    help="for ncu: set up the tuned plan, then run one step (or one PCG launch set, or one build) "
+                         "inside an NVTX range of that name, and exit")
     return ap.parse_args()
 
 
@@ -636,6 +639,7 @@ def mpc_comparison(args, torch, sspcg, stream, rank, net=None, sample=32):
                                           "if it came from HBM (an upper bound on the HBM rate)"}}
         allx = b.lambdas()
         lams[mode] = [allx[i] for i in idx]
+    out["single_reduction"] = implicit_comparison(args, torch, sspcg, stream, probs, b, gammas)
     stats = sspcg.plan_stats(plan)
     last = [dataclasses.replace(probs[i], gamma=P.perturb_gamma(probs[i], R)) for i in idx]
     res = {"workload": w.name, "problems": len(probs), "resolves": R, "generate_seconds": round(gen_s, 1),
@@ -655,6 +659,43 @@ def build_bytes(probs) -> int:
         n, N, m, u = p.N + 1, p.N, p.nx, p.nu
         tot += N * m * m + N * m * u + n * m + N * u + 2 * (n * m * m + N * m * m)
     return 4 * tot
+
+
+def implicit_comparison(args, torch, sspcg, stream, probs, b, gammas, resolves=3):
+    """Single-reduction (Chronopoulos-Gear) PCG on the MPC workload, with the symmetric stair applied explicitly
+    (PD and PE blocks) or implicitly, Phi_sym^-1 = 2 D^-1 - D^-1 S D^-1: block-Jacobi D^-1 with the degree-1
+    polynomial and no PE blocks.  Re-solves from lambda0 = 0 on the blocks the MPC section built (its PD is
+    D^-1 for both), each plan autotuned for its own launch shapes."""
+    d = b.dev
+    out = {}
+    for name, kind, deg, pe in (("explicit", "sym", 0, b.PE), ("implicit", "bj", 1, None)):
+        plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
+                                       sspcg.options(tol=P.MPC_BATCH_16384.tol, cg_variant=1, poly_degree=deg))
+        lam = torch.zeros_like(b.lam); it = torch.zeros_like(b.iters); rr = torch.zeros_like(b.relres)
+        st = torch.zeros_like(b.status)
+        D2, E2 = torch.zeros_like(b.D), torch.zeros_like(b.E)
+        PD2, PE2 = torch.zeros_like(b.PD), torch.zeros_like(b.PE)
+        sspcg.sspcg_plan_autotune(plan, kind, d["A"], d["B"], d["qd"], d["rd"], gammas[0], D2, E2, PD2, PE2, lam, it,
+                                  rr, st, stream, which="solve")
+        del D2, E2, PD2, PE2
+        ms, iters, ok = 0.0, [], True
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for r in range(1, resolves + 1):
+            lam.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sspcg.sspcg_solve_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.PD, pe, gammas[r], lam, it, rr, st,
+                                         stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            iters.append(float(it.cpu().numpy().mean()))
+            ok &= bool((st.cpu().numpy() == 0).all())
+        out[name] = {"solves_per_s": len(probs) * resolves / (ms / 1e3), "ms_per_resolve": ms / resolves,
+                     "iters_mean": round(float(np.mean(iters)), 2), "all_converged": ok}
+        del plan
+    out["implicit_vs_explicit"] = out["implicit"]["solves_per_s"] / out["explicit"]["solves_per_s"]
+    return out
 
 
 def main():
@@ -699,6 +740,31 @@ def main():
 
     def step():
         sspcg.sspcg_plan_launch(plan, stream)
+
+    if args.profile:
+        # one profiled region (ncu --nvtx --nvtx-include "<name>/"), after one untimed step
+        it_p = torch.zeros_like(b.iters); rr_p = torch.zeros_like(b.relres); st_p = torch.zeros_like(b.status)
+        lam_p = torch.zeros_like(b.lam)
+        fn = {"step": step,
+              "pcg": lambda: sspcg.sspcg_solve_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE,
+                                                          d["gamma"], lam_p, it_p, rr_p, st_p, stream),
+              "build": lambda: (sspcg.sspcg_build_schur_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.D, b.E,
+                                                                stream),
+                                sspcg.sspcg_build_precond_batched(plan, PRECOND, b.D, b.E, b.PD, b.PE, st_p, stream))}
+        with torch.cuda.stream(stream):
+            fn[args.profile]()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(args.profile)
+        with torch.cuda.stream(stream):
+            fn[args.profile]()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        its = (it_p if args.profile == "pcg" else b.iters).cpu().numpy().astype(np.int64)
+        alg = sum(int(its[i]) * algorithmic_bytes_per_iteration(p) for i, p in enumerate(probs))
+        print(json.dumps({"profile": args.profile, "problems": nprob, "iters_sum": int(its.sum()),
+                          "pcg_algorithmic_bytes": alg, "build_bytes": build_bytes(probs),
+                          "pcg_launches": sspcg.plan_stats(plan)["solve_qp_launches"]}), flush=True)
+        return
 
     with torch.cuda.stream(stream):
         for _ in range(warm):

@@ -145,8 +145,11 @@ typedef struct {
                               Gear 1989): the same iterates in exact arithmetic, s = S p kept by recurrence,
                               and (r.u, S u.u, r.r) in one block sum per iteration (one barrier and one
                               reduction tree fewer).  Run by the QP-form FP32 solves; requires
-                              SSPCG_REDUCE_DF and poly_degree = 0 (SSPCG_ERR_INVALID_ARG otherwise); the
-                              FP64 and block-form solves stay textbook.  iters counts x updates either way. */
+                              SSPCG_REDUCE_DF (SSPCG_ERR_INVALID_ARG otherwise); the FP64 and block-form
+                              solves stay textbook.  With poly_degree d > 0, u = Phi_d^-1 r as above.  With
+                              block-Jacobi blocks, d = 1 and no PE this applies the symmetric stair
+                              implicitly, Phi_sym^-1 = 2 D^-1 - D^-1 S D^-1 (Sec. IV with Eq. stair_inv), with
+                              one reduction per iteration.  iters counts x updates either way. */
 } sspcg_options;
 
 #define SSPCG_MAX_POLY_DEGREE 16
@@ -199,6 +202,11 @@ sspcg_status sspcg_build_precond(int32_t N, int32_t nx, sspcg_precond kind, cons
  * Outputs (device, 1 element each): iters = number of S*p products,
  * relres = ||r||_2 / ||gamma||_2 of the recurrence residual, status.
  * gamma = 0 gives lambda = 0, iters = 0.
+ * PE may be NULL: the preconditioner is then block-diagonal (block-Jacobi,
+ * or Jacobi's diagonal blocks), and its off-diagonal blocks are neither
+ * staged nor read; the same holds for every solve entry point below and for
+ * the pipelines with SSPCG_PRECOND_BLOCK_JACOBI or SSPCG_PRECOND_JACOBI,
+ * which pass no PE to their solves.
  */
 sspcg_status sspcg_solve(int32_t N, int32_t nx, const float *D, const float *E, const float *PD, const float *PE,
                          const float *gamma, float *lambda, const sspcg_options *opts, int32_t *iters,

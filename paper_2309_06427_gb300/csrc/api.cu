@@ -118,7 +118,7 @@ sspcg_status validate_opts(const sspcg_options *o) {
   if (o->precision < 0 || o->precision > 2) return SSPCG_ERR_INVALID_ARG;
   if (o->poly_degree < 0 || o->poly_degree > SSPCG_MAX_POLY_DEGREE) return SSPCG_ERR_INVALID_ARG;
   if (o->cg_variant < 0 || o->cg_variant > 1) return SSPCG_ERR_INVALID_ARG;
-  if (o->cg_variant == 1 && (o->reduction != SSPCG_REDUCE_DF || o->poly_degree != 0)) return SSPCG_ERR_INVALID_ARG;
+  if (o->cg_variant == 1 && o->reduction != SSPCG_REDUCE_DF) return SSPCG_ERR_INVALID_ARG;
   return SSPCG_OK;
 }
 
@@ -618,7 +618,7 @@ static sspcg_status solve_single(int op, bool f64, int32_t N, int32_t nx, int32_
                                  sspcg_stream stream) {
   if (validate_opts(opts) != SSPCG_OK) return SSPCG_ERR_INVALID_ARG;
   if (!shape_ok(N, nx, nu)) return SSPCG_ERR_INVALID_ARG;
-  if (!PD || !gamma || !lambda || !iters || !relres || !status || (N > 0 && !PE)) return SSPCG_ERR_INVALID_ARG;
+  if (!PD || !gamma || !lambda || !iters || !relres || !status) return SSPCG_ERR_INVALID_ARG;  // PE may be NULL
   if (op == kOpQp && (!qd || (N > 0 && (!A || !rd || (nu > 0 && !B))))) return SSPCG_ERR_INVALID_ARG;
   if (op == kOpBlock && (!D || (N > 0 && !E))) return SSPCG_ERR_INVALID_ARG;
   int K = 0;
@@ -967,8 +967,7 @@ static sspcg_status check_solve_args(sspcg_plan *plan, int op, const float *A, c
                                      const float *rd, const float *D, const float *E, const float *PD,
                                      const float *PE, const float *gamma, float *lambda, int32_t *iters,
                                      double *relres, int32_t *status) {
-  if (!PD || !gamma || !lambda || !iters || !relres || !status) return SSPCG_ERR_INVALID_ARG;
-  if (plan->total_off > 0 && !PE) return SSPCG_ERR_INVALID_ARG;
+  if (!PD || !gamma || !lambda || !iters || !relres || !status) return SSPCG_ERR_INVALID_ARG;  // PE may be NULL
   if (op == kOpQp && (!qd || (plan->total_off > 0 && (!A || !rd || !B)))) return SSPCG_ERR_INVALID_ARG;
   if (op == kOpBlock && (!D || (plan->total_off > 0 && !E))) return SSPCG_ERR_INVALID_ARG;
   return SSPCG_OK;
@@ -1053,15 +1052,18 @@ static sspcg_status pipeline_build(sspcg_plan *plan, sspcg_precond kind, const f
 static sspcg_status pipeline_solve(sspcg_plan *plan, const float *A, const float *B, const float *qd,
                                    const float *rd, const float *gamma, const float *PD, const float *PE,
                                    float *lambda, int32_t *iters, double *relres, int32_t *status, int warm,
-                                   sspcg_stream stream) {
+                                   sspcg_stream stream, bool diag_only = false) {
   cudaStream_t st = (cudaStream_t)stream;
   time_mark(plan, 1, st);
-  PcgArgs a32 = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
+  // block-Jacobi and Jacobi: the off-diagonal blocks are zero, so the solves neither stage nor read them
+  PcgArgs a32 = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, diag_only ? nullptr : PE, gamma, lambda, iters,
+                             relres, status);
   a32.warm = warm;
   PcgArgs a64 = a32;
   a64.ps = tiny_set(plan);
   a64.PD = plan->PD64;
-  a64.PE = plan->PE64;
+  a64.PE = diag_only ? nullptr : plan->PE64;
+
 
   sspcg_status s = launch_sets(plan, {{&plan->sets[kSetQpMain], a32}, {&plan->sets[kSetTiny], a64}}, st);
   time_mark(plan, 2, st);
@@ -1082,7 +1084,7 @@ sspcg_status sspcg_pipeline_batched(sspcg_plan *plan, sspcg_precond kind, const 
   s = pipeline_build(plan, kind, A, B, qd, rd, D, E, PD, PE, status, stream);
   if (s != SSPCG_OK) return s;
   return pipeline_solve(plan, A, B, qd, rd, gamma, PD, PE, lambda, iters, relres, status, plan->opts.warm_start,
-                        stream);
+                        stream, kind == SSPCG_PRECOND_BLOCK_JACOBI || kind == SSPCG_PRECOND_JACOBI);
 }
 
 sspcg_status sspcg_plan_capture_pipeline(sspcg_plan *plan, sspcg_precond kind, const float *A, const float *B,
@@ -1220,12 +1222,16 @@ sspcg_status sspcg_plan_autotune(sspcg_plan *plan, int32_t which, sspcg_precond 
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) {
-    PcgArgs a32 = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
+    // block-Jacobi and Jacobi: time the solves without off-diagonal blocks, as the pipeline runs them
+    const bool diag_only = kind == SSPCG_PRECOND_BLOCK_JACOBI || kind == SSPCG_PRECOND_JACOBI;
+    PcgArgs a32 = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, diag_only ? nullptr : PE, gamma, lambda,
+                               iters, relres, status);
     a32.warm = 0;
     PcgArgs a64 = a32;
     a64.ps = tiny_set(plan);
     a64.PD = plan->PD64;
-    a64.PE = plan->PE64;
+    a64.PE = diag_only ? nullptr : plan->PE64;
+
     if (which & SSPCG_TUNE_PIPELINE) {
       s = tune_set(plan, plan->sets[kSetQpMain], plan->hdesc, a32, status0, st, e0, e1);
       if (s == SSPCG_OK) s = tune_set(plan, plan->sets[kSetTiny], plan->tdesc, a64, status0, st, e0, e1);

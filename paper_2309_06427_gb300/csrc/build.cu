@@ -73,15 +73,38 @@ __global__ void __launch_bounds__(kBuildWarps * 32) schur_build_kernel(ProbSet p
     }
     for (int i = lane; i < nx; i += 32) sIq[i] = Real(1) / (Real)qk[i];
     __syncwarp();
-    for (int e = lane; e < nn; e += 32) {
-      const int i = e / nx, j = e - i * nx;
-      if (i > j) continue;
-      Real s = Real(0);
-      for (int l = 0; l < nx; ++l) s = fma(sAQ[i * nx + l], sA[j * nx + l], s);
-      for (int m = 0; m < nu; ++m) s = fma(sBR[i * nu + m], sB[j * nu + m], s);
-      if (i == j) s += sIq[i];
-      Dk[i * nx + j] = s;
-      Dk[j * nx + i] = s;
+    // upper triangle in tiles of four entries of one row, (i, j0..j0+3) with j0 = i + 4 t: each lane keeps four
+    // accumulators and loads the row-i factor once per term; every entry sums its terms in the same order
+    // as a one-entry loop would (l = 0..nx-1, then m = 0..nu-1)
+    const int ntiles = (nx * (nx + 1) / 2 + 3 * nx) / 4 + nx;  // an upper bound; tiles past the end are skipped
+    for (int tl = lane; tl < ntiles; tl += 32) {
+      int i = 0, rem = tl;
+      while (i < nx && rem >= (nx - i + 3) / 4) rem -= (nx - i + 3) / 4, ++i;
+      if (i >= nx) break;
+      const int j0 = i + 4 * rem;
+      int jj[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) jj[q] = min(j0 + q, nx - 1);
+      Real s[4] = {Real(0), Real(0), Real(0), Real(0)};
+      for (int l = 0; l < nx; ++l) {
+        const Real a = sAQ[i * nx + l];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] = fma(a, sA[jj[q] * nx + l], s[q]);
+      }
+      for (int m = 0; m < nu; ++m) {
+        const Real b = sBR[i * nu + m];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] = fma(b, sB[jj[q] * nu + m], s[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = j0 + q;
+        if (j >= nx) break;
+        Real v = s[q];
+        if (i == j) v += sIq[i];
+        Dk[i * nx + j] = v;
+        Dk[j * nx + i] = v;
+      }
     }
     __syncwarp();
   }
@@ -385,18 +408,43 @@ __global__ void __launch_bounds__(kBuildWarps * 32) precond_off_kernel(ProbSet p
       sP0[e] = P0[e];
     }
     __syncwarp();
-    for (int e = lane; e < nn; e += 32) {
-      const int i = e / nx, j = e - i * nx;
-      Real s = Real(0);
-      for (int t = 0; t < nx; ++t) s = fma(sP1[i * nx + t], sE[t * nx + j], s);
-      sT[e] = s;
+    // both products in tiles of four entries of one row, (i, 4 t .. 4 t + 3): four accumulators per lane, the
+    // row factor loaded once per term; each entry sums t = 0..nx-1 in order, as a one-entry loop would
+    const int cw = (nx + 3) / 4, ntl = nx * cw;
+    for (int tl = lane; tl < ntl; tl += 32) {
+      const int i = tl / cw, j0 = 4 * (tl - i * cw);
+      int jj[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) jj[q] = min(j0 + q, nx - 1);
+      Real s[4] = {Real(0), Real(0), Real(0), Real(0)};
+      for (int t = 0; t < nx; ++t) {
+        const Real a = sP1[i * nx + t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] = fma(a, sE[t * nx + jj[q]], s[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (j0 + q < nx) sT[i * nx + j0 + q] = s[q];
     }
     __syncwarp();
-    for (int e = lane; e < nn; e += 32) {
-      const int i = e / nx, j = e - i * nx;
-      Real s = Real(0);
-      for (int t = 0; t < nx; ++t) s = fma(sT[i * nx + t], sP0[t * nx + j], s);
-      PEk[e] = -c * s;
+    for (int tl = lane; tl < ntl; tl += 32) {
+      const int i = tl / cw, j0 = 4 * (tl - i * cw);
+      int jj[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) jj[q] = min(j0 + q, nx - 1);
+      Real s[4] = {Real(0), Real(0), Real(0), Real(0)};
+      for (int t = 0; t < nx; ++t) {
+        const Real a = sT[i * nx + t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] = fma(a, sP0[t * nx + jj[q]], s[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = j0 + q;
+        if (j >= nx) break;
+        const Real v = -c * s[q];
+        PEk[i * nx + j] = v;
+      }
     }
     __syncwarp();
   }

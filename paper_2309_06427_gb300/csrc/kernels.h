@@ -130,6 +130,7 @@ struct PcgArgs {
 // block rows as fit in ``smem`` bytes (at most a.max_resident).
 cudaError_t launch_pcg(int nx, int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
                        cudaStream_t st);
+
 int pcg_max_smem_bytes();
 // CTAs of that PCG variant that fit on one SM at ``block`` threads and ``smem`` bytes of dynamic shared memory
 // (registers, threads and shared memory; gv: vectors in a global workspace; cg: single-reduction PCG).

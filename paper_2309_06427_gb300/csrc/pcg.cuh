@@ -203,6 +203,8 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   }
   if (OP == kOpQp)
     for (int e = tid; e < NUP; e += T) svu[e - NUP] = Real(0);
+  // no off-diagonal preconditioner blocks (PE == nullptr): the preconditioner is block-diagonal
+  const bool diag_only = a.PE == nullptr;
   const float *gam = a.gamma + d.ovec;
   // lambda (global): read once for a warm start, written once at the end
   auto lam_load = [&](int row) -> Real {
@@ -229,8 +231,8 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   {
     Real *spd = sm + L.pd, *spe = sm + L.pe;
     stage_blocks<NX>(spd, V.gPD, K, V.ld, tid, T);
-    stage_blocks<NX>(spe, V.gPE, Ks, V.ld, tid, T);
-    if (N == 0)  // the zero off-diagonal slot of a single knot
+    if (!diag_only) stage_blocks<NX>(spe, V.gPE, Ks, V.ld, tid, T);
+    if (N == 0 && !diag_only)  // the zero off-diagonal slot of a single knot
       for (int e = tid; e < NX * V.ld; e += T) spe[e] = Real(0);
     V.sPD = spd; V.sPE = spe;
   }
@@ -339,8 +341,40 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     }
   };
   auto apply_P_row = [&](const Real *src, int k, int i) -> Real {
+    if (diag_only) {  // block-diagonal preconditioner: the diagonal block only (symmetric; read by column)
+      Seg<NX, Real> s;
+      s.load(src + k * NXP);
+      return k < K ? dot_seg<NX, true, Real>(V.sPD + k * NX * V.ld + i, V.ld, s.v)
+                   : dot_seg<NX, false, Real>(V.gPD + (int64_t)k * NX * NX + i, NX, s.v);
+    }
     return k < K ? bt_row<NX, true, Real>(V.sPD, V.sPE, V.ld, N, k, i, src)
                  : bt_row<NX, false, Real>(V.gPD, V.gPE, NX, N, k, i, src);
+  };
+
+  // dst = Phi_d^-1 sr (polynomial of degree d = poly, Horner correction form as in ``precondition``); ends
+  // with a barrier.  The single-reduction variant's preconditioning step.
+  auto precondition_into = [&](Real *dst) {
+    for (int row = tid; row < R_; row += T) {
+      int k, i;
+      const int si = vid(row, k, i);
+      dst[si] = apply_P_row(sr, k, i);
+    }
+    for (int t = 0; t < poly; ++t) {
+      __syncthreads();  // dst complete
+      apply_S_phase1(dst);
+      for (int row = tid; row < R_; row += T) {
+        int k, i;
+        const int si = vid(row, k, i);
+        se[si] = sr[si] - apply_S_row(dst, k, i);
+      }
+      __syncthreads();  // e complete
+      for (int row = tid; row < R_; row += T) {
+        int k, i;
+        const int si = vid(row, k, i);
+        dst[si] = dst[si] + apply_P_row(se, k, i);
+      }
+    }
+    __syncthreads();
   };
 
   // sw = z = Phi_d^-1 sr (polynomial of degree d = poly), and the block sums (r.z, r.r) into rz_, rr_.
@@ -427,12 +461,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     // since p.S p = S u.u - beta (r.u)new / alpha for the new p.  iters counts x updates, as textbook.
     Real ru = Real(0), del = Real(0), rr = Real(0);  // r.u, S u.u, r.r
     auto u_w_sums = [&]() {
-      for (int row = tid; row < R_; row += T) {
-        int k, i;
-        const int si = vid(row, k, i);  // sets k, i: its own statement, before they are read
-        su[si] = apply_P_row(sr, k, i);
-      }
-      __syncthreads();
+      precondition_into(su);  // u = Phi_d^-1 r
       apply_S_phase1(su);
       AccT s3[3] = {R::zero(), R::zero(), R::zero()};
       for (int row = tid; row < R_; row += T) {

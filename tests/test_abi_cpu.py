@@ -58,9 +58,8 @@ def test_invalid_shapes_rejected_on_host(L):
         bad = sspcg.options(poly_degree=deg)
         assert L.sspcg_solve(4, 4, vp, vp, vp, vp, vp, vp, ctypes.byref(bad), vp, vp, vp, None) == \
             sspcg.ERR_INVALID_ARG
-    # single-reduction PCG: variant 0 or 1, double-float sums, no polynomial
-    for bad in (sspcg.options(cg_variant=2), sspcg.options(cg_variant=1, reduction="f32"),
-                sspcg.options(cg_variant=1, poly_degree=1)):
+    # single-reduction PCG: variant 0 or 1, double-float sums (polynomial preconditioners are allowed)
+    for bad in (sspcg.options(cg_variant=2), sspcg.options(cg_variant=1, reduction="f32")):
         assert L.sspcg_solve(4, 4, vp, vp, vp, vp, vp, vp, ctypes.byref(bad), vp, vp, vp, None) == \
             sspcg.ERR_INVALID_ARG
     # plan with a bad shape
