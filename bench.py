@@ -116,9 +116,10 @@ def parse():
     ap.add_argument("--no-mpc", action="store_true", help="skip the MPC workload (16384 problems, 10 re-solves)")
     ap.add_argument("--mpc-resolves", type=int, default=10)
     ap.add_argument("--mpc-problems", type=int, default=0, help="first N problems of the MPC batch; 0: all")
-    ap.add_argument("--profile", choices=["step", "pcg", "build"], default=None,
-                    help="for ncu: set up the tuned plan, then run one step (or one PCG launch set, or one build) "
-                         "inside an NVTX range of that name, and exit")
+    ap.add_argument("--profile", choices=["step", "pcg", "build", "mpc"], default=None,
+                    help="for ncu: set up the tuned plan, then run one step (or one PCG launch set, one build, or "
+                         "one PCG launch set of the MPC batch, --mpc-problems of it) inside an NVTX range of that "
+                         "name, and exit")
     return ap.parse_args()
 
 
@@ -651,6 +652,54 @@ def mpc_comparison(args, torch, sspcg, stream, rank, net=None, sample=32):
     return res, last, lams
 
 
+def one_time_bytes(probs) -> int:
+    """Bytes one PCG launch set must move at least once: read A, B, diag Q, R, PD, PE and gamma, write lambda
+    (FP32).  DRAM traffic near this figure means every block was read from HBM once per solve."""
+    tot = 0
+    for p in probs:
+        n, N, m, u = p.N + 1, p.N, p.nx, p.nu
+        tot += N * m * m + N * m * u + n * m + N * u + n * m * m + N * m * m + 2 * n * m
+    return 4 * tot
+
+
+def profile_mpc(args, torch, sspcg, stream):
+    """One PCG launch set of the MPC batch (its first ``--mpc-problems`` problems, from lambda0 = 0, autotuned)
+    inside the NVTX range "mpc", after one untimed launch set."""
+    w = P.MPC_BATCH_16384
+    count = args.mpc_problems if args.mpc_problems > 0 else w.nprob
+    probs = P.make_workload_parallel(w, count=count, start=0)
+    plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
+                                   sspcg.options(tol=w.tol))
+    b = sspcg.Batch(plan, probs)
+    d = b.dev
+    sspcg.sspcg_plan_autotune(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD, b.PE,
+                              b.lam, b.iters, b.relres, b.status, stream, which="solve")
+    with torch.cuda.stream(stream):
+        sspcg.sspcg_build_schur_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.D, b.E, stream)
+        sspcg.sspcg_build_precond_batched(plan, PRECOND, b.D, b.E, b.PD, b.PE, b.status, stream)
+
+    def solve():
+        b.lam.zero_()
+        sspcg.sspcg_solve_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE, d["gamma"], b.lam, b.iters,
+                                     b.relres, b.status, stream)
+
+    with torch.cuda.stream(stream):
+        solve()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("mpc")
+    with torch.cuda.stream(stream):
+        solve()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    its = b.iters.cpu().numpy().astype(np.int64)
+    alg = sum(int(its[i]) * algorithmic_bytes_per_iteration(p) for i, p in enumerate(probs))
+    stats = sspcg.plan_stats(plan)
+    print(json.dumps({"profile": "mpc", "problems": len(probs), "iters_sum": int(its.sum()),
+                      "pcg_algorithmic_bytes": alg, "one_time_bytes": one_time_bytes(probs),
+                      "pcg_launches": stats["solve_qp_launches"], "streamed_problems": stats["solve_qp_stream"],
+                      "all_converged": bool((b.status.cpu().numpy() == 0).all())}), flush=True)
+
+
 def build_bytes(probs) -> int:
     """HBM bytes the two build calls must move at least: read A, B, diag Q, diag R once, write the Schur blocks
     D, E and the preconditioner blocks PD, PE once (FP32)."""
@@ -713,6 +762,10 @@ def main():
     _build.build()
     from paper_2309_06427_gb300 import sspcg
 
+    if args.profile == "mpc":
+        profile_mpc(args, torch, sspcg, torch.cuda.Stream())
+        return
+
     w = WORKLOAD
     nprob = args.problems if args.problems > 0 else w.nprob
     probs = P.make_workload(w, count=nprob, start=rank_start(rank, nprob))  # weak scaling
@@ -762,7 +815,8 @@ def main():
         its = (it_p if args.profile == "pcg" else b.iters).cpu().numpy().astype(np.int64)
         alg = sum(int(its[i]) * algorithmic_bytes_per_iteration(p) for i, p in enumerate(probs))
         print(json.dumps({"profile": args.profile, "problems": nprob, "iters_sum": int(its.sum()),
-                          "pcg_algorithmic_bytes": alg, "build_bytes": build_bytes(probs),
+                          "pcg_algorithmic_bytes": alg, "one_time_bytes": one_time_bytes(probs),
+                          "build_bytes": build_bytes(probs),
                           "pcg_launches": sspcg.plan_stats(plan)["solve_qp_launches"]}), flush=True)
         return
 
@@ -895,7 +949,8 @@ def main():
                          "resident_fp32_problems": stats["pipeline_resident"],
                          "streamed_fp32_problems": stats["pipeline_stream"], "fp64_problems": stats["pipeline_f64"],
                          "pcg_launches_per_step": stats["pipeline_launches"],
-                         "groups": [{k: g[k] for k in ("nx", "cls", "problems", "max_N", "block", "grid", "stream")}
+                         "groups": [{k: g[k] for k in ("nx", "cls", "problems", "max_N", "block", "grid", "stream",
+                                                       "share")}
                                     for g in sched]}
 
     # the FP64 reduction mode beside the double-float default

@@ -396,7 +396,8 @@ sspcg_status sspcg_plan_launch(sspcg_plan *plan, sspcg_stream stream);
  * per nx and residency class), times candidate schedules alone on these
  * inputs: block sizes 64..512 threads (16 rows per thread to one) and,
  * for groups that do not fit in shared memory whole, staging the first rows
- * or streaming every block row from L2.  Each group keeps its fastest
+ * into the whole budget or into 1/2, 1/3 or 1/4 of it (several CTAs per
+ * SM), or streaming every block row from L2.  Each group keeps its fastest
  * candidate (grid from the kernel's occupancy at that block size); the
  * choices also go to a process-wide cache keyed by (launch set, operator form,
  * precision, reduction, polynomial degree, PCG variant, nx, residency class,
@@ -416,7 +417,7 @@ sspcg_status sspcg_plan_autotune(sspcg_plan *plan, int32_t which, sspcg_precond 
                                  sspcg_stream stream);
 
 /* Fields per group of sspcg_plan_schedule. */
-#define SSPCG_SCHEDULE_FIELDS 9
+#define SSPCG_SCHEDULE_FIELDS 10
 /*
  * The PCG launch groups of a plan: which = 0 (the pipeline's FP32 set),
  * 1 (its FP64 set), 2 (sspcg_solve_qp_batched).  *count = number of groups;
@@ -424,7 +425,8 @@ sspcg_status sspcg_plan_autotune(sspcg_plan *plan, int32_t which, sspcg_precond 
  * out: nx, residency class (0 partially staged, 1..4 fully staged, 5
  * vectors in global memory), problems, largest N, block threads, grid CTAs,
  * dynamic shared memory bytes, streams every block row (0/1), chosen by the
- * tuner or its cache (0/1).
+ * tuner or its cache (0/1), shared-memory share (a partially staged group
+ * stages into 1/share of the budget, so up to share CTAs fit on an SM).
  */
 sspcg_status sspcg_plan_schedule(const sspcg_plan *plan, int32_t which, int32_t *out, int32_t capacity,
                                  int32_t *count);

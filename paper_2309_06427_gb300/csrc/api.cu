@@ -87,9 +87,12 @@ int auto_block(int64_t rows) {
 // Staged block rows K and dynamic shared memory (bytes) of a PCG problem
 // under a schedule; false when even the vectors do not fit.
 // cg: the options ask for single-reduction PCG, which the QP-form FP32 launches run (two more vectors).
-bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int poly, int cg, int *K, int64_t *bytes) {
+// share: the problem's CTA gets 1/share of the dynamic shared-memory budget (share > 1 lets several CTAs of a
+// partially staged group share an SM, each staging fewer block rows).
+bool pcg_fit(int op, int sched, int N, int nx, int nu, bool f64, int poly, int cg, int *K, int64_t *bytes,
+             int share = 1) {
   const int64_t esz = f64 ? sizeof(double) : sizeof(float);
-  const int64_t budget = smem_budget() / esz;
+  const int64_t budget = smem_budget() / share / esz;
   cg = (cg && op == kOpQp && !f64) ? 1 : 0;
   int k = pcg_max_resident(op, N, nx, nu, budget, poly > 0, cg);
   if (k < 0) return false;
@@ -158,6 +161,7 @@ struct PcgGroup {
   bool f64 = false;
   bool gvec = false;         // vectors in a global workspace (slot_elems per CTA from scratch_off)
   bool stream = false;       // stage no block rows (the schedule option, or the tuner's choice)
+  int share = 1;             // partially staged groups: stage into 1/share of the shared memory (tuner's choice)
   bool tuned = false;        // block and residency from the tuner (this plan's, or its cache)
   int64_t slot_elems = 0, scratch_off = 0;
   int max_grid = 0;          // global-vector groups: CTAs the workspace holds
@@ -312,6 +316,7 @@ struct TuneKey {
 struct TuneChoice {
   int block;
   bool stream;
+  int share;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune_cache;
@@ -341,7 +346,8 @@ sspcg_status shape_group(const sspcg_plan *p, const GroupSet &set, PcgGroup &g, 
       b = gvec_slot(set.op, d.N, d.nx, d.nu, p->opts.poly_degree, cg);
     } else {
       const int sched = g.stream ? SSPCG_SCHED_STREAM : p->opts.schedule;
-      if (!pcg_fit(set.op, sched, d.N, d.nx, d.nu, set.f64, p->opts.poly_degree, cg, &K, &b)) return SSPCG_ERR_UNSUPPORTED;
+      if (!pcg_fit(set.op, sched, d.N, d.nx, d.nu, set.f64, p->opts.poly_degree, cg, &K, &b, g.stream ? 1 : g.share))
+        return SSPCG_ERR_UNSUPPORTED;
     }
     maxbytes = std::max(maxbytes, b);
   }
@@ -420,6 +426,7 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
         if (it != g_tune_cache.end()) {
           g.block = it->second.block;
           g.stream = it->second.stream && r == 0;
+          g.share = r == 0 ? it->second.share : 1;
           g.tuned = true;
         }
       }
@@ -1168,13 +1175,22 @@ sspcg_status tune_set(sspcg_plan *p, GroupSet &set, const std::vector<ProbDesc> 
     // from at most 16 rows per thread to at most one
     const int64_t max_block = std::max<int64_t>(64, round_up(g.maxrows, 32));
     const int64_t min_block = std::min<int64_t>(max_block, g.maxrows / 16);
-    for (int stream = 0; stream <= (g.cls == 0 ? 1 : 0); ++stream) {
+    // residency candidates: partially staged groups may stage into 1/2 .. 1/4 of the shared memory (several
+    // CTAs per SM) or stream every block row; the other classes keep their staging
+    for (int cand = 0; cand < (g.cls == 0 ? 5 : 1); ++cand) {
+      const bool stream = cand == 4;
+      const int share = cand < 4 ? cand + 1 : 1;
       for (int blk : kBlocks) {
-        if (blk > max_block || blk < min_block || (blk == orig.block && (stream != 0) == orig.stream)) continue;
+        if (blk > max_block || blk < min_block ||
+            (blk == orig.block && stream == orig.stream && share == orig.share))
+          continue;
         PcgGroup c = orig;
         c.block = blk;
-        c.stream = stream != 0;
-        if ((s = shape_group(p, set, c, descs)) != SSPCG_OK) return s;
+        c.stream = stream;
+        c.share = share;
+        s = shape_group(p, set, c, descs);
+        if (s == SSPCG_ERR_UNSUPPORTED) continue;  // the vectors do not fit in that share
+        if (s != SSPCG_OK) return s;
         float ms = 0.0f;
         if ((s = time_group(p, set, c, base, status0, st, e0, e1, &ms)) != SSPCG_OK) return s;
         if (ms < best_ms) {
@@ -1186,7 +1202,7 @@ sspcg_status tune_set(sspcg_plan *p, GroupSet &set, const std::vector<ProbDesc> 
     g = best;
     g.tuned = true;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[tune_key(p, set, g)] = TuneChoice{g.block, g.stream};
+    g_tune_cache[tune_key(p, set, g)] = TuneChoice{g.block, g.stream, g.share};
   }
   return SSPCG_OK;
 }
@@ -1260,7 +1276,7 @@ sspcg_status sspcg_plan_schedule(const sspcg_plan *plan, int32_t which, int32_t 
     const PcgGroup &g = set.groups[i];
     int32_t *r = out + (int64_t)i * SSPCG_SCHEDULE_FIELDS;
     r[0] = g.nx; r[1] = g.cls; r[2] = g.nwork; r[3] = g.maxN; r[4] = g.block; r[5] = g.grid;
-    r[6] = (int32_t)g.smem; r[7] = g.stream ? 1 : 0; r[8] = g.tuned ? 1 : 0;
+    r[6] = (int32_t)g.smem; r[7] = g.stream ? 1 : 0; r[8] = g.tuned ? 1 : 0; r[9] = g.share;
   }
   return SSPCG_OK;
 }

@@ -497,10 +497,11 @@ cudaError_t launch_precond_inv(const ProbSet &ps, const int2 *refs, int64_t tota
   cudaError_t e = smem_attr_once(attr4, precond_inv_kernel<Real, 4>, 210 * 1024);
   if (e == cudaSuccess) e = smem_attr_once(attr8, precond_inv_kernel<Real, 8>, 210 * 1024);
   if (e != cudaSuccess) return e;
-  // lanes per knot: 8 for the larger blocks, 4 otherwise; knots per CTA limited by 200 KB of shared memory
+  // lanes per knot: 8 for the larger blocks, 4 otherwise; knots per CTA limited by 112 KB of shared memory, so
+  // that two CTAs fit on an SM (about 28 warps per SM for nx = 21 instead of 16)
   const int G = nx >= 16 ? 8 : 4;
   const int per_knot = (inv_stride(nx) + nx) * (int)sizeof(double);
-  int knots = (int)std::min<int64_t>(512 / G, (200 * 1024) / per_knot);
+  int knots = (int)std::min<int64_t>(512 / G, (112 * 1024) / per_knot);
   knots = std::max(32 / G, knots / (32 / G) * (32 / G));  // whole warps
   const int threads = knots * G;
   const size_t smem = kind == 3 ? 0 : (size_t)knots * per_knot;

@@ -315,7 +315,7 @@ def sspcg_plan_autotune(plan: Plan, kind, A, B, qd, rd, gamma, D, E, PD, PE, lam
                                      _ptr(status), _stream(stream)), "sspcg_plan_autotune")
 
 
-SCHEDULE_FIELDS = ("nx", "cls", "problems", "max_N", "block", "grid", "smem", "stream", "tuned")
+SCHEDULE_FIELDS = ("nx", "cls", "problems", "max_N", "block", "grid", "smem", "stream", "tuned", "share")
 
 
 def sspcg_plan_schedule(plan: Plan, which: str = "pipeline") -> List[Dict[str, int]]:

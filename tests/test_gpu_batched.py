@@ -239,6 +239,7 @@ def test_autotuned_plan_matches_heuristic_plan():
     assert max(rel(lt[i], xs[i]) for i in range(len(probs))) <= LAMBDA_RTOL
     plan_c = _plan(probs)
     sc = sspcg.sspcg_plan_schedule(plan_c)
-    assert [(g["block"], g["stream"], g["tuned"]) for g in sc] == [(g["block"], g["stream"], 1) for g in sched["pipeline"]]
+    assert ([(g["block"], g["stream"], g["share"], g["tuned"]) for g in sc] ==
+            [(g["block"], g["stream"], g["share"], 1) for g in sched["pipeline"]])
     sspcg.sspcg_autotune_cache_clear()
     assert not any(g["tuned"] for g in sspcg.sspcg_plan_schedule(_plan(probs)))
