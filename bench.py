@@ -114,6 +114,8 @@ def parse():
     ap.add_argument("--train-gammas", type=int, default=49,
                     help="right-hand sides per training problem (its own gamma and seeded N(0, 1) draws)")
     ap.add_argument("--no-mpc", action="store_true", help="skip the MPC workload (16384 problems, 10 re-solves)")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the small-problem batch (one problem per CTA against one problem per warp)")
     ap.add_argument("--mpc-resolves", type=int, default=10)
     ap.add_argument("--mpc-problems", type=int, default=0, help="first N problems of the MPC batch; 0: all")
     ap.add_argument("--profile", choices=["step", "pcg", "build", "mpc"], default=None,
@@ -700,6 +702,37 @@ def profile_mpc(args, torch, sspcg, stream):
                       "all_converged": bool((b.status.cpu().numpy() == 0).all())}), flush=True)
 
 
+def small_problems_comparison(args, torch, sspcg, stream, steps=5):
+    """The small-problem batch (16384 problems, N ~ U{8..32}, nx in {2, 4, 6}: more problems than the GPU holds
+    at one problem per CTA), whole pipeline step: the untuned schedule (one problem per CTA), the autotuned one
+    (whose candidates include one problem per warp) and the "warp" schedule (one problem per warp, as many
+    warps per CTA as fit), each with its own plan, timed like the headline step."""
+    w = P.SMALL_BATCH_16384
+    probs = P.make_workload_parallel(w)
+    out = {"workload": w.name, "problems": len(probs)}
+    for name, sched, tune in (("cta", "auto", False), ("tuned", "auto", True), ("warp", "warp", False)):
+        if tune:
+            sspcg.sspcg_autotune_cache_clear()
+        plan = sspcg.sspcg_plan_create([p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs],
+                                       sspcg.options(tol=w.tol, schedule=sched))
+        b = sspcg.Batch(plan, probs)
+        d = b.dev
+        if tune:
+            sspcg.sspcg_plan_autotune(plan, PRECOND, d["A"], d["B"], d["qd"], d["rd"], d["gamma"], b.D, b.E, b.PD,
+                                      b.PE, b.lam, b.iters, b.relres, b.status, stream, which="pipeline")
+        ms = timed_steps(torch, stream, lambda: b.pipeline(PRECOND, stream), steps, 3)
+        sched_rows = sspcg.sspcg_plan_schedule(plan) + sspcg.sspcg_plan_schedule(plan, "pipeline_f64")
+        out[name] = {"solves_per_s": len(probs) / (ms / 1e3), "ms_per_step": ms,
+                     "iters_mean": float(b.iters.cpu().numpy().mean()),
+                     "all_converged": bool((b.status.cpu().numpy() == 0).all()),
+                     "groups_one_problem_per_warp": sum(1 for g in sched_rows if g["warps"] > 0),
+                     "groups": len(sched_rows)}
+        del b, plan
+    sspcg.sspcg_autotune_cache_clear()
+    out["warp_vs_cta"] = out["warp"]["solves_per_s"] / out["cta"]["solves_per_s"]
+    return out
+
+
 def build_bytes(probs) -> int:
     """HBM bytes the two build calls must move at least: read A, B, diag Q, diag R once, write the Schur blocks
     D, E and the preconditioner blocks PD, PE once (FP32)."""
@@ -950,7 +983,7 @@ def main():
                          "streamed_fp32_problems": stats["pipeline_stream"], "fp64_problems": stats["pipeline_f64"],
                          "pcg_launches_per_step": stats["pipeline_launches"],
                          "groups": [{k: g[k] for k in ("nx", "cls", "problems", "max_N", "block", "grid", "stream",
-                                                       "share")}
+                                                       "share", "warps")}
                                     for g in sched]}
 
     # the FP64 reduction mode beside the double-float default
@@ -1010,6 +1043,8 @@ def main():
             gpu_lams[f"warm_start_ragged.{name}"] = ("ragged", [lw[i] for i in sample3])
         r3["speedup"] = r3["warm"]["solves_per_s"] / r3["plain"]["solves_per_s"]
         line["warm_start_ragged"] = r3
+    if not args.no_small:
+        line["small_problems"] = small_problems_comparison(args, torch, sspcg, stream)
     if not args.no_mpc:
         mpc, mpc_probs, mpc_lams = mpc_comparison(args, torch, sspcg, stream, rank, net)
         line["mpc"] = mpc

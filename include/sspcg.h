@@ -116,6 +116,10 @@ enum {
   SSPCG_SCHED_RESIDENT = 1, /* operator and preconditioner staged once into shared memory (as many block
                                rows as fit; the rest read from L2/HBM every iteration) */
   SSPCG_SCHED_STREAM = 2,   /* operator and preconditioner read from L2/HBM every iteration */
+  SSPCG_SCHED_WARP = 3,     /* plan calls: as RESIDENT, and every group of problems that fit whole in shared
+                               memory (QP operator form, textbook PCG, double-float or FP64 sums) runs one
+                               problem per warp, as many warps per CTA as fit (at most 16); other entry
+                               points: as RESIDENT */
 };
 
 /* Solver options. */
@@ -417,7 +421,7 @@ sspcg_status sspcg_plan_autotune(sspcg_plan *plan, int32_t which, sspcg_precond 
                                  sspcg_stream stream);
 
 /* Fields per group of sspcg_plan_schedule. */
-#define SSPCG_SCHEDULE_FIELDS 10
+#define SSPCG_SCHEDULE_FIELDS 11
 /*
  * The PCG launch groups of a plan: which = 0 (the pipeline's FP32 set),
  * 1 (its FP64 set), 2 (sspcg_solve_qp_batched).  *count = number of groups;
@@ -426,7 +430,9 @@ sspcg_status sspcg_plan_autotune(sspcg_plan *plan, int32_t which, sspcg_precond 
  * vectors in global memory), problems, largest N, block threads, grid CTAs,
  * dynamic shared memory bytes, streams every block row (0/1), chosen by the
  * tuner or its cache (0/1), shared-memory share (a partially staged group
- * stages into 1/share of the budget, so up to share CTAs fit on an SM).
+ * stages into 1/share of the budget, so up to share CTAs fit on an SM),
+ * warps per CTA when each warp solves its own problem (0: one problem per
+ * CTA).
  */
 sspcg_status sspcg_plan_schedule(const sspcg_plan *plan, int32_t which, int32_t *out, int32_t capacity,
                                  int32_t *count);

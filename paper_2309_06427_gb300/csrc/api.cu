@@ -115,7 +115,7 @@ sspcg_status validate_opts(const sspcg_options *o) {
   if (!(o->tol >= 0.0)) return SSPCG_ERR_INVALID_ARG;
   if (o->warm_start < 0 || o->warm_start > 2) return SSPCG_ERR_INVALID_ARG;
   if (o->reduction < 0 || o->reduction > 2) return SSPCG_ERR_INVALID_ARG;
-  if (o->schedule < 0 || o->schedule > 2) return SSPCG_ERR_INVALID_ARG;
+  if (o->schedule < 0 || o->schedule > 3) return SSPCG_ERR_INVALID_ARG;
   if (o->block_threads != 0 && (o->block_threads < 32 || o->block_threads > 512 || o->block_threads % 32))
     return SSPCG_ERR_INVALID_ARG;
   if (o->precision < 0 || o->precision > 2) return SSPCG_ERR_INVALID_ARG;
@@ -162,6 +162,7 @@ struct PcgGroup {
   bool gvec = false;         // vectors in a global workspace (slot_elems per CTA from scratch_off)
   bool stream = false;       // stage no block rows (the schedule option, or the tuner's choice)
   int share = 1;             // partially staged groups: stage into 1/share of the shared memory (tuner's choice)
+  int warps = 0;             // > 0: one problem per warp, this many warps per CTA (tuner's choice; see warp_ok)
   bool tuned = false;        // block and residency from the tuner (this plan's, or its cache)
   int64_t slot_elems = 0, scratch_off = 0;
   int max_grid = 0;          // global-vector groups: CTAs the workspace holds
@@ -317,6 +318,7 @@ struct TuneChoice {
   int block;
   bool stream;
   int share;
+  int warps;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune_cache;
@@ -330,6 +332,14 @@ int n_bucket(int32_t maxN) {
 TuneKey tune_key(const sspcg_plan *p, const GroupSet &set, const PcgGroup &g) {
   return TuneKey{set.id, set.op, set.f64 ? 1 : 0, set.f64 ? kRedF64 : red_mode(p->opts.reduction), p->opts.poly_degree,
                  (p->opts.cg_variant && set.op == kOpQp && !set.f64) ? 1 : 0, g.nx, g.cls, n_bucket(g.maxN)};
+}
+
+// One problem per warp exists for fully staged groups of the QP form with textbook PCG: the FP64 path, and
+// FP32 with double-float sums.
+bool warp_ok(const sspcg_plan *p, const GroupSet &set, const PcgGroup &g) {
+  if (set.op != kOpQp || g.gvec || g.cls < 1 || g.cls > 4) return false;
+  if (set.f64) return true;
+  return red_mode(p->opts.reduction) == kRedDf && p->opts.cg_variant == 0;
 }
 
 // Dynamic shared memory, slot size and grid of a group for its block size and residency: every member's
@@ -353,7 +363,20 @@ sspcg_status shape_group(const sspcg_plan *p, const GroupSet &set, PcgGroup &g, 
   }
   int ctas = 0;
   const bool cgv = cg && set.op == kOpQp && !set.f64;
-  cudaError_t e = occupancy_pcg(g.nx, set.op, red, set.f64, g.gvec, cgv, g.block, g.gvec ? 0 : (size_t)maxbytes, &ctas);
+  if (g.warps > 0) {  // one problem per warp: a slot of maxbytes (16-byte multiple) per warp
+    const int64_t slot = round_up(maxbytes, 16);
+    if (slot * g.warps > smem_budget()) return SSPCG_ERR_UNSUPPORTED;
+    g.block = 32 * g.warps;
+    cudaError_t e = occupancy_pcg(g.nx, set.op, red, set.f64, false, cgv, true, g.block, (size_t)(slot * g.warps),
+                                  &ctas);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (ctas < 1) return SSPCG_ERR_UNSUPPORTED;
+    g.smem = (size_t)(slot * g.warps);
+    g.grid = (int)std::min<int64_t>((g.nwork + g.warps - 1) / g.warps, (int64_t)ctas * device_sms());
+    return SSPCG_OK;
+  }
+  cudaError_t e = occupancy_pcg(g.nx, set.op, red, set.f64, g.gvec, cgv, false, g.block,
+                                g.gvec ? 0 : (size_t)maxbytes, &ctas);
   if (e != cudaSuccess) return cuda_fail(e);
   ctas = std::max(1, ctas);
   if (g.gvec) {
@@ -427,8 +450,17 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
           g.block = it->second.block;
           g.stream = it->second.stream && r == 0;
           g.share = r == 0 ? it->second.share : 1;
+          g.warps = warp_ok(p, set, g) ? it->second.warps : 0;
           g.tuned = true;
         }
+      }
+      if (p->opts.schedule == SSPCG_SCHED_WARP && warp_ok(p, set, g)) {
+        // one problem per warp: as many warps (a power of two, at most 16) as slots of the largest member fit
+        int64_t slot = 0;
+        for (int32_t i : b) slot = std::max(slot, round_up(bytes[i], 16));
+        const int64_t fit = slot > 0 ? smem_budget() / slot : 1;
+        g.warps = 1;
+        while (g.warps < 16 && 2 * g.warps <= fit) g.warps *= 2;
       }
       if (g.gvec) {
         // two CTAs per SM at most: each holds a workspace slot (about 7 (N+1) nx values)
@@ -441,6 +473,10 @@ sspcg_status plan_groups(sspcg_plan *p, GroupSet &set, const std::vector<ProbDes
         set.scratch_elems += (int64_t)g.max_grid * g.slot_elems;
       }
       sspcg_status s = shape_group(p, set, g, descs);
+      if (s == SSPCG_ERR_UNSUPPORTED && g.warps > 0) {  // a cached warp count whose slots do not fit this group
+        g.warps = 0;
+        s = shape_group(p, set, g, descs);
+      }
       if (s != SSPCG_OK) return s;
       g.d_work = p->d_work + pos;
       g.counter_index = p->ngroups_total++;
@@ -510,6 +546,7 @@ sspcg_status launch_sets(sspcg_plan *p, std::initializer_list<SetLaunch> list, c
     a.counter = p->d_counters + g.counter_index;
     set_gvec(a, p, *all[i].set, g);
     if (g.stream) a.max_resident = 0;
+    a.warp = g.warps > 0 ? 1 : 0;
     cudaStream_t s = i == 0 ? st : p->side[i - 1];
     const int red = g.f64 ? kRedF64 : red_mode(p->opts.reduction);
     SSPCG_CUDA(launch_pcg(g.nx, all[i].set->op, red, g.f64, a, g.grid, g.block, g.smem, s));
@@ -1144,6 +1181,7 @@ sspcg_status time_group(sspcg_plan *p, const GroupSet &set, const PcgGroup &g, c
   a.counter = p->d_counters + g.counter_index;
   set_gvec(a, p, set, g);
   if (g.stream) a.max_resident = 0;
+  a.warp = g.warps > 0 ? 1 : 0;
   const int red = g.f64 ? kRedF64 : red_mode(p->opts.reduction);
   float best = 1e30f;
   for (int rep = 0; rep < 3; ++rep) {
@@ -1199,10 +1237,28 @@ sspcg_status tune_set(sspcg_plan *p, GroupSet &set, const std::vector<ProbDesc> 
         }
       }
     }
+    // fully staged groups: one problem per warp, 1 .. 16 warps per CTA (as many as fit in the budget)
+    if (warp_ok(p, set, orig)) {
+      for (int w : {1, 2, 4, 8, 16}) {
+        PcgGroup c = orig;
+        c.warps = w;
+        c.stream = false;
+        c.share = 1;
+        s = shape_group(p, set, c, descs);
+        if (s == SSPCG_ERR_UNSUPPORTED) break;  // w slots do not fit
+        if (s != SSPCG_OK) return s;
+        float ms = 0.0f;
+        if ((s = time_group(p, set, c, base, status0, st, e0, e1, &ms)) != SSPCG_OK) return s;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+    }
     g = best;
     g.tuned = true;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[tune_key(p, set, g)] = TuneChoice{g.block, g.stream, g.share};
+    g_tune_cache[tune_key(p, set, g)] = TuneChoice{g.block, g.stream, g.share, g.warps};
   }
   return SSPCG_OK;
 }
@@ -1276,7 +1332,7 @@ sspcg_status sspcg_plan_schedule(const sspcg_plan *plan, int32_t which, int32_t 
     const PcgGroup &g = set.groups[i];
     int32_t *r = out + (int64_t)i * SSPCG_SCHEDULE_FIELDS;
     r[0] = g.nx; r[1] = g.cls; r[2] = g.nwork; r[3] = g.maxN; r[4] = g.block; r[5] = g.grid;
-    r[6] = (int32_t)g.smem; r[7] = g.stream ? 1 : 0; r[8] = g.tuned ? 1 : 0; r[9] = g.share;
+    r[6] = (int32_t)g.smem; r[7] = g.stream ? 1 : 0; r[8] = g.tuned ? 1 : 0; r[9] = g.share; r[10] = g.warps;
   }
   return SSPCG_OK;
 }

@@ -123,6 +123,7 @@ struct PcgArgs {
   int32_t max_resident;  // cap on staged block rows (a schedule override); large = no cap
   void *gscratch;        // vectors in global memory: CTA b uses gscratch + b * gstride elements
   int64_t gstride;       //   (nullptr: vectors in shared memory)
+  int32_t warp;          // 1: one problem per warp (smem_elems per warp), QP form, textbook PCG
 };
 
 // PCG launch for one nx; dispatches to the instantiation for that nx.
@@ -133,8 +134,10 @@ cudaError_t launch_pcg(int nx, int op, int red, bool f64, const PcgArgs &a, int 
 
 int pcg_max_smem_bytes();
 // CTAs of that PCG variant that fit on one SM at ``block`` threads and ``smem`` bytes of dynamic shared memory
-// (registers, threads and shared memory; gv: vectors in a global workspace; cg: single-reduction PCG).
-cudaError_t occupancy_pcg(int nx, int op, int red, bool f64, bool gv, bool cg, int block, size_t smem, int *ctas);
+// (registers, threads and shared memory; gv: vectors in a global workspace; cg: single-reduction PCG;
+// warp: one problem per warp).
+cudaError_t occupancy_pcg(int nx, int op, int red, bool f64, bool gv, bool cg, bool warp, int block, size_t smem,
+                          int *ctas);
 
 // Schur build and preconditioner assembly; Real = float (FP32 blocks) or
 // double (the FP64 path).  refs[i] = (problem, block row) of work item i

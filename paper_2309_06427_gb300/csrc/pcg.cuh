@@ -32,6 +32,7 @@
 // and are converted exactly; Phi^-1 blocks, vectors and lambda are Real.
 #pragma once
 
+#include <cstring>
 #include <type_traits>
 
 #include "common.cuh"
@@ -96,6 +97,27 @@ __device__ __forceinline__ void block_sum(typename R::T (&v)[K], typename R::T *
   for (int e = 0; e < K; ++e) v[e] = R::sum(lane < nw ? slots[e * 32 + lane] : R::zero());
 }
 
+// The thread group that solves one problem: the CTA, or one warp (WARP: several problems per CTA, one per
+// warp, with warp barriers and warp-only reductions).  A warp's xor butterfly leaves the same sum in every
+// lane (each step adds the same two values in both lanes of a pair), so the scalars stay bit-identical across
+// the group as in block_sum.
+template <bool WARP>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+
+template <class R, int K, bool WARP>
+__device__ __forceinline__ void group_sum(typename R::T (&v)[K], typename R::T *slots) {
+  if constexpr (WARP) {
+#pragma unroll
+    for (int e = 0; e < K; ++e) v[e] = R::sum(v[e]);
+    __syncwarp();
+  } else {
+    block_sum<R, K>(v, slots);
+  }
+}
+
 // A block-row segment of a vector in registers: NXP = nx rounded up to 4
 // entries, loaded with 128-bit shared-memory loads (the segment starts
 // 16-byte aligned; entries past nx are padding and never used).
@@ -154,12 +176,40 @@ __device__ __forceinline__ Real bt_row(const MT *Md, const MT *Mo, int ld, int N
   return (a + b) + c;
 }
 
+// Staging: the first ``count`` elements of a dense row-major array with rows of width w (global) into shared
+// memory rows of stride ld, converted to Real.  With a 16-byte aligned source (the packed layout aligns every
+// problem's arrays) each thread takes 16 consecutive bytes per load (four FP32 or two FP64 values) and
+// scatters them into the padded rows; the rest, or an unaligned source, one element at a time.
+template <typename Real, typename T>
+__device__ __forceinline__ void stage_rows(Real *dst, const T *src, int count, int w, int ld, int tid, int nthr) {
+  constexpr int per = 16 / (int)sizeof(T);
+  int done = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    const int nv = count / per;
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    for (int v = tid; v < nv; v += nthr) {
+      const float4 c = __ldg(s4 + v);
+      T vals[per];
+      memcpy(vals, &c, sizeof(c));
+      const int e = v * per;
+      int r = e / w, col = e - r * w;
+#pragma unroll
+      for (int q = 0; q < per; ++q) {
+        dst[r * ld + col] = (Real)vals[q];
+        if (++col == w) { col = 0; ++r; }
+      }
+    }
+    done = nv * per;
+  }
+  for (int e = done + tid; e < count; e += nthr) {
+    const int r = e / w, col = e - r * w;
+    dst[r * ld + col] = (Real)__ldg(src + e);
+  }
+}
+
 template <int NX, typename Real>
 __device__ __forceinline__ void stage_blocks(Real *dst, const Real *src, int nblk, int ld, int tid, int T) {
-  for (int e = tid; e < nblk * NX * NX; e += T) {
-    const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
-    dst[(b * NX + r) * ld + c] = src[e];
-  }
+  stage_rows(dst, src, nblk * NX * NX, NX, ld, tid, T);
 }
 
 // Operator and preconditioner blocks of one problem: the first K block rows
@@ -174,14 +224,14 @@ struct Views {
   int ld, ldb;                                    // staged row strides
 };
 
-template <int NX, int OP, int RED, typename Real, bool CG = false>
+template <int NX, int OP, int RED, typename Real, bool CG = false, bool WARP = false>
 __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typename Red<RED, Real>::T *slots) {
   using R = Red<RED, Real>;
   using AccT = typename R::T;
   constexpr int NXP = (NX + 3) & ~3;
   const int p = d.id;  // output slot
   const int N = d.N, n = N + 1, nu = d.nu, R_ = n * NX, NUP = vec_stride(nu);
-  const int tid = threadIdx.x, T = blockDim.x;
+  const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x, T = WARP ? 32 : (int)blockDim.x;
   const int poly = a.poly;
   int K = pcg_max_resident(OP, N, NX, nu, a.smem_elems, poly > 0, CG);  // the host sized smem so that K >= 0
   if (K > a.max_resident) K = a.max_resident;
@@ -242,14 +292,8 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     V.gA = a.A + d.oA;
     V.gB = a.B + d.oB;
     Real *s0 = sm + L.m0, *s1 = sm + L.m1;
-    for (int e = tid; e < Ks * NX * NX; e += T) {
-      const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
-      s0[(b * NX + r) * V.ld + c] = (Real)V.gA[e];
-    }
-    for (int e = tid; e < Ks * NX * nu; e += T) {
-      const int row = e / nu, c = e - row * nu;
-      s1[row * V.ldb + c] = (Real)V.gB[e];
-    }
+    stage_rows(s0, V.gA, Ks * NX * NX, NX, V.ld, tid, T);
+    if (nu > 0) stage_rows(s1, V.gB, Ks * NX * nu, nu, V.ldb, tid, T);
     if (N == 0) {  // the zero off-diagonal slot of a single knot
       for (int e = tid; e < NX * V.ld; e += T) s0[e] = Real(0);
       for (int e = tid; e < NX * V.ldb; e += T) s1[e] = Real(0);
@@ -267,14 +311,8 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     V.gD = a.D + d.odiag;
     V.gE = a.E + d.ooff;
     Real *s0 = sm + L.m0, *s1 = sm + L.m1;
-    for (int e = tid; e < K * NX * NX; e += T) {
-      const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
-      s0[(b * NX + r) * V.ld + c] = (Real)V.gD[e];
-    }
-    for (int e = tid; e < Ks * NX * NX; e += T) {
-      const int b = e / (NX * NX), rem = e - b * NX * NX, r = rem / NX, c = rem - r * NX;
-      s1[(b * NX + r) * V.ld + c] = (Real)V.gE[e];
-    }
+    stage_rows(s0, V.gD, K * NX * NX, NX, V.ld, tid, T);
+    stage_rows(s1, V.gE, Ks * NX * NX, NX, V.ld, tid, T);
     if (N == 0)  // the zero off-diagonal slot of a single knot
       for (int e = tid; e < NX * V.ld; e += T) s1[e] = Real(0);
     V.sD = s0; V.sE = s1;
@@ -309,7 +347,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
           svu[k * NUP + j] = acc * sir[k * NUP + j];
         }
       }
-      __syncthreads();
+      group_sync<WARP>();
     }
   };
   // Row (k, i) of S src (QP form: of C sv).
@@ -360,21 +398,21 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       dst[si] = apply_P_row(sr, k, i);
     }
     for (int t = 0; t < poly; ++t) {
-      __syncthreads();  // dst complete
+      group_sync<WARP>();  // dst complete
       apply_S_phase1(dst);
       for (int row = tid; row < R_; row += T) {
         int k, i;
         const int si = vid(row, k, i);
         se[si] = sr[si] - apply_S_row(dst, k, i);
       }
-      __syncthreads();  // e complete
+      group_sync<WARP>();  // e complete
       for (int row = tid; row < R_; row += T) {
         int k, i;
         const int si = vid(row, k, i);
         dst[si] = dst[si] + apply_P_row(se, k, i);
       }
     }
-    __syncthreads();
+    group_sync<WARP>();
   };
 
   // sw = z = Phi_d^-1 sr (polynomial of degree d = poly), and the block sums (r.z, r.r) into rz_, rr_.
@@ -392,14 +430,14 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       s2[1] = R::fma(s2[1], r, r);
     }
     for (int t = 0; t < poly; ++t) {
-      __syncthreads();  // z complete
+      group_sync<WARP>();  // z complete
       apply_S_phase1(sw);
       for (int row = tid; row < R_; row += T) {
         int k, i;
         const int si = vid(row, k, i);
         se[si] = sr[si] - apply_S_row(sw, k, i);
       }
-      __syncthreads();  // e complete
+      group_sync<WARP>();  // e complete
       const bool last = t + 1 == poly;
       for (int row = tid; row < R_; row += T) {
         int k, i;
@@ -409,12 +447,12 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
         if (last) s2[0] = R::fma(s2[0], sr[si], z);
       }
     }
-    block_sum<R, 2>(s2, slots + 64);
+    group_sum<R, 2, WARP>(s2, slots + 64);
     rz_ = R::get(s2[0]);
     rr_ = R::get(s2[1]);
   };
 
-  __syncthreads();  // staged blocks and reciprocals visible
+  group_sync<WARP>();  // staged blocks and reciprocals visible
 
   // ---- r0 = gamma - S x0, z0 = Phi^-1 r0, p0 = z0 ----
   AccT g1[1] = {R::zero()};
@@ -427,14 +465,14 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     sp[si] = x0;
     sx[si] = x0;
   }
-  block_sum<R, 1>(g1, slots);  // contains a barrier: sp complete
+  group_sum<R, 1, WARP>(g1, slots);  // contains a barrier: sp complete
   const Real gg = R::get(g1[0]);
   const Real thresh = (Real)a.tol2 * gg;
   const int max_iter = a.max_iter > 0 ? a.max_iter : 10 * n * NX;
   if (gg == Real(0)) {
     for (int row = tid; row < R_; row += T) lam_store(row, Real(0));
     if (tid == 0) { a.iters[p] = 0; a.relres[p] = 0.0; a.status[p] = kOk; }
-    __syncthreads();
+    group_sync<WARP>();
     return;
   }
   bool warm = a.warm != 0;
@@ -451,7 +489,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       sr[vid(row, k, i)] = (Real)gam[row];
     }
   }
-  __syncthreads();
+  group_sync<WARP>();
   if constexpr (CG) {
     // Single-reduction PCG (Chronopoulos & Gear 1989): the same iterates as the textbook algorithm, with
     // s = S p kept by recurrence, so that r.u, S u.u and r.r come from one block sum per iteration:
@@ -474,7 +512,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
         s3[1] = R::fma(s3[1], w, u);
         s3[2] = R::fma(s3[2], r, r);
       }
-      block_sum<R, 3>(s3, slots);
+      group_sum<R, 3, WARP>(s3, slots);
       ru = R::get(s3[0]);
       del = R::get(s3[1]);
       rr = R::get(s3[2]);
@@ -489,7 +527,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
           sx[si] = Real(0);
         }
         warm = false;
-        __syncthreads();
+        group_sync<WARP>();
         continue;
       }
       break;
@@ -513,7 +551,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
         sx[si] = rfma(alpha, pn, sx[si]);
         sr[si] = rfma(-alpha, sn, sr[si]);
       }
-      __syncthreads();
+      group_sync<WARP>();
       const Real ru_old = ru;
       u_w_sums();
       ++it;
@@ -532,7 +570,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       a.relres[p] = sqrt((double)rr / (double)gg);
       a.status[p] = code;
     }
-    __syncthreads();
+    group_sync<WARP>();
     return;
   }
   Real rz, rr;
@@ -547,7 +585,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
         sx[si] = Real(0);
       }
       warm = false;
-      __syncthreads();
+      group_sync<WARP>();
       continue;
     }
     break;
@@ -557,7 +595,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     const int si = vid(row, k, i);
     sp[si] = sw[si];
   }
-  __syncthreads();
+  group_sync<WARP>();
 
   // ---- iterations ----
   int it = 0, code = kOk;
@@ -577,7 +615,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       sw[si] = w;
       s1[0] = R::fma(s1[0], sp[si], w);
     }
-    block_sum<R, 1>(s1, slots);
+    group_sum<R, 1, WARP>(s1, slots);
     const Real pw = R::get(s1[0]);
     if (!(pw > Real(0)) || !isfinite(pw)) { code = isfinite(pw) ? kBreakdown : kNonFinite; break; }
     const Real alpha = rz / pw;
@@ -587,7 +625,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       sx[si] = rfma(alpha, sp[si], sx[si]);
       sr[si] = rfma(-alpha, sw[si], sr[si]);
     }
-    __syncthreads();
+    group_sync<WARP>();
     // z = Phi_d^-1 r, r.z, r.r
     Real rz_new;
     precondition(rz_new, rr);
@@ -598,7 +636,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       const int si = vid(row, k, i);
       sp[si] = rfma(beta, sp[si], sw[si]);
     }
-    __syncthreads();
+    group_sync<WARP>();
     ++it;
   }
   for (int row = tid; row < R_; row += T) {
@@ -610,14 +648,16 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
     a.relres[p] = sqrt((double)rr / (double)gg);
     a.status[p] = code;
   }
-  __syncthreads();
+  group_sync<WARP>();
 }
 
 // Persistent kernel: CTAs take problems from the work list, through an
 // atomic counter when one is given (largest problems first), else by stride.
 // GV: vectors in this CTA's slot of a global workspace (problems whose vectors do not fit in shared
 // memory).  A compile-time choice, so that the other launches address their vectors as shared memory.
-template <int NX, int OP, int RED, typename Real, bool GV, bool CG = false>
+// WARP: every warp takes its own problems (one warp per problem, several per CTA); warp w of the CTA works in
+// shared-memory slot w of a.smem_elems elements.
+template <int NX, int OP, int RED, typename Real, bool GV, bool CG = false, bool WARP = false>
 __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
   extern __shared__ float4 smem4[];
   Real *sm;
@@ -626,44 +666,71 @@ __global__ void __launch_bounds__(512) pcg_kernel(PcgArgs a) {
   __shared__ __align__(16) typename Red<RED, Real>::T slots[4 * 32];
   __shared__ int s_next;
   int stride_i = 0;
-  while (true) {
-    int w;
-    if (a.counter) {
-      if (threadIdx.x == 0) s_next = atomicAdd(a.counter, 1);
-      __syncthreads();
-      w = s_next;
-      __syncthreads();
-    } else {
-      w = blockIdx.x + stride_i * gridDim.x;
-      ++stride_i;
+  if constexpr (WARP) {
+    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    Real *wsm = sm + (int64_t)wid * a.smem_elems;
+    while (true) {
+      int w;
+      if (a.counter) {
+        int t = 0;
+        if ((threadIdx.x & 31) == 0) t = atomicAdd(a.counter, 1);
+        w = __shfl_sync(0xffffffffu, t, 0);
+      } else {
+        w = (blockIdx.x * nw + wid) + stride_i * gridDim.x * nw;
+        ++stride_i;
+      }
+      if (w >= a.nwork) break;
+      const ProbDesc d = a.ps.get(a.work ? a.work[w] : w);
+      if (a.status[d.id] != kOk) continue;  // preconditioner failed for this problem
+      pcg_solve<NX, OP, RED, Real, CG, true>(a, d, wsm, nullptr);
     }
-    if (w >= a.nwork) break;
-    const ProbDesc d = a.ps.get(a.work ? a.work[w] : w);
-    if (a.status[d.id] != kOk) continue;  // preconditioner failed for this problem
-    pcg_solve<NX, OP, RED, Real, CG>(a, d, sm, slots);
+  } else {
+    while (true) {
+      int w;
+      if (a.counter) {
+        if (threadIdx.x == 0) s_next = atomicAdd(a.counter, 1);
+        __syncthreads();
+        w = s_next;
+        __syncthreads();
+      } else {
+        w = blockIdx.x + stride_i * gridDim.x;
+        ++stride_i;
+      }
+      if (w >= a.nwork) break;
+      const ProbDesc d = a.ps.get(a.work ? a.work[w] : w);
+      if (a.status[d.id] != kOk) continue;  // preconditioner failed for this problem
+      pcg_solve<NX, OP, RED, Real, CG>(a, d, sm, slots);
+    }
   }
 }
 
 // One compiled variant of the PCG kernel: its launch and its occupancy (CTAs per SM for a block size and
 // dynamic shared memory, registers included).  The shared-memory attribute is set once per device.
-template <int NX, int OP, int RED, typename Real, bool GV, bool CG>
+// WARP launches split the dynamic shared memory into one slot per warp (a multiple of 16 bytes each).
+template <int NX, int OP, int RED, typename Real, bool GV, bool CG, bool WARP = false>
 struct PcgVariant {
   static cudaError_t prepare() {
     static std::atomic<uint64_t> attr_done{0};
-    return smem_attr_once(attr_done, pcg_kernel<NX, OP, RED, Real, GV, CG>, pcg_max_smem_bytes());
+    return smem_attr_once(attr_done, pcg_kernel<NX, OP, RED, Real, GV, CG, WARP>, pcg_max_smem_bytes());
   }
   static cudaError_t launch(const PcgArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
     PcgArgs b = a;
-    b.smem_elems = (int64_t)(smem / sizeof(Real));
-    pcg_kernel<NX, OP, RED, Real, GV, CG><<<grid, block, smem, st>>>(b);
+    if constexpr (WARP) {
+      if (block % 32 != 0) return cudaErrorInvalidValue;
+      b.smem_elems = (int64_t)((smem / (size_t)(block / 32)) & ~(size_t)15) / (int64_t)sizeof(Real);
+    } else {
+      b.smem_elems = (int64_t)(smem / sizeof(Real));
+    }
+    pcg_kernel<NX, OP, RED, Real, GV, CG, WARP><<<grid, block, smem, st>>>(b);
     return cudaGetLastError();
   }
   static cudaError_t occupancy(int block, size_t smem, int *ctas) {
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, pcg_kernel<NX, OP, RED, Real, GV, CG>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, pcg_kernel<NX, OP, RED, Real, GV, CG, WARP>, block,
+                                                         smem);
   }
 };
 
@@ -671,8 +738,16 @@ struct PcgVariant {
 // for both operator forms, and the FP64 path (QP form, FP64 reductions); vectors in a global workspace (gv)
 // for the QP form only; single-reduction PCG (cg) for the QP form with FP32 arithmetic and double-float sums.
 // f(PcgVariant<...>{}) is called on it; cudaErrorInvalidValue when no variant exists.
+// warp: one problem per warp, for the QP form with textbook PCG: FP32 with double-float sums, and the FP64
+// path.
 template <int NX, typename F>
-cudaError_t with_pcg_variant(int op, int red, bool f64, bool gv, bool cg, F &&f) {
+cudaError_t with_pcg_variant(int op, int red, bool f64, bool gv, bool cg, bool warp, F &&f) {
+  if (warp) {
+    if (op != kOpQp || gv || (cg && !f64)) return cudaErrorInvalidValue;
+    if (f64) return f(PcgVariant<NX, kOpQp, kRedF64, double, false, false, true>{});
+    if (red == kRedDf) return f(PcgVariant<NX, kOpQp, kRedDf, float, false, false, true>{});
+    return cudaErrorInvalidValue;
+  }
   if (cg && op == kOpQp && !f64) {  // single-reduction PCG (the FP64 and block-form launches stay textbook)
     if (red != kRedDf) return cudaErrorInvalidValue;
     if (gv) return f(PcgVariant<NX, kOpQp, kRedDf, float, true, true>{});
@@ -705,13 +780,14 @@ cudaError_t with_pcg_variant(int op, int red, bool f64, bool gv, bool cg, F &&f)
 template <int NX>
 cudaError_t launch_pcg_for_nx(int op, int red, bool f64, const PcgArgs &a, int grid, int block, size_t smem,
                               cudaStream_t st) {
-  return with_pcg_variant<NX>(op, red, f64, a.gscratch != nullptr, a.cg != 0,
+  return with_pcg_variant<NX>(op, red, f64, a.gscratch != nullptr, a.cg != 0, a.warp != 0,
                               [&](auto v) { return decltype(v)::launch(a, grid, block, smem, st); });
 }
 
 template <int NX>
-cudaError_t occupancy_pcg_for_nx(int op, int red, bool f64, bool gv, bool cg, int block, size_t smem, int *ctas) {
-  return with_pcg_variant<NX>(op, red, f64, gv, cg,
+cudaError_t occupancy_pcg_for_nx(int op, int red, bool f64, bool gv, bool cg, bool warp, int block, size_t smem,
+                                 int *ctas) {
+  return with_pcg_variant<NX>(op, red, f64, gv, cg, warp,
                               [&](auto v) { return decltype(v)::occupancy(block, smem, ctas); });
 }
 
@@ -723,8 +799,8 @@ cudaError_t occupancy_pcg_for_nx(int op, int red, bool f64, bool gv, bool cg, in
                                  cudaStream_t st) {                                                          \
     return launch_pcg_for_nx<NXV>(op, red, f64, a, grid, block, smem, st);                                    \
   }                                                                                                          \
-  cudaError_t occupancy_pcg_nx##NXV(int op, int red, bool f64, bool gv, bool cg, int block, size_t smem,       \
-                                    int *ctas) {                                                             \
-    return occupancy_pcg_for_nx<NXV>(op, red, f64, gv, cg, block, smem, ctas);                                \
+  cudaError_t occupancy_pcg_nx##NXV(int op, int red, bool f64, bool gv, bool cg, bool warp, int block,        \
+                                    size_t smem, int *ctas) {                                                \
+    return occupancy_pcg_for_nx<NXV>(op, red, f64, gv, cg, warp, block, smem, ctas);                          \
   }                                                                                                          \
   }

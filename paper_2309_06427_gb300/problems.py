@@ -144,8 +144,11 @@ WARMSTART_EVAL_4096 = Workload("warm-start eval 4096 problems nx=14 nu=7 N=64", 
 MPC_BATCH_16384 = Workload("MPC batch 16384 problems N~U{64..512} nx~U{4..28}", 5, 16384, 0.05, 1e-6,
                            N_range=(64, 512), nx_range=(4, 28))
 
+# many small problems (more than the GPU holds at once at one problem per CTA): the case for one problem per warp
+SMALL_BATCH_16384 = Workload("small batch 16384 problems N~U{8..32} nx in {2,4,6}", 6, 16384, 0.05, 1e-6,
+                             N_range=(8, 32), nx_set=(2, 4, 6))
 WORKLOADS = {w.config: w for w in (PENDULUM_SINGLE, MANIPULATOR_SINGLE, RAGGED_BATCH_4096,
-                                   WARMSTART_EVAL_4096, MPC_BATCH_16384)}
+                                   WARMSTART_EVAL_4096, MPC_BATCH_16384, SMALL_BATCH_16384)}
 
 
 def problem_shape(w: Workload, index: int) -> tuple:

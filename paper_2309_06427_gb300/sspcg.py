@@ -21,7 +21,7 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA = 0, 1, 2, 3
 SOLVE_OK, SOLVE_MAXITER, SOLVE_BREAKDOWN, SOLVE_NOT_SPD, SOLVE_NONFINITE = 0, 1, 2, 3, 4
 PRECOND = {"sym": 0, "add": 1, "bj": 2, "jacobi": 3}
 REDUCE = {"df": 0, "f32": 1, "f64": 2}
-SCHED = {"auto": 0, "resident": 1, "stream": 2}
+SCHED = {"auto": 0, "resident": 1, "stream": 2, "warp": 3}
 PRECISION = {"auto": 0, "f32": 1, "f64": 2}
 ARRAY_A, ARRAY_B, ARRAY_QD, ARRAY_RD, ARRAY_DIAG, ARRAY_OFF, ARRAY_VEC, ARRAY_RFULL = range(8)
 NUM_ARRAYS = 8
@@ -315,7 +315,7 @@ def sspcg_plan_autotune(plan: Plan, kind, A, B, qd, rd, gamma, D, E, PD, PE, lam
                                      _ptr(status), _stream(stream)), "sspcg_plan_autotune")
 
 
-SCHEDULE_FIELDS = ("nx", "cls", "problems", "max_N", "block", "grid", "smem", "stream", "tuned", "share")
+SCHEDULE_FIELDS = ("nx", "cls", "problems", "max_N", "block", "grid", "smem", "stream", "tuned", "share", "warps")
 
 
 def sspcg_plan_schedule(plan: Plan, which: str = "pipeline") -> List[Dict[str, int]]:

@@ -239,7 +239,46 @@ def test_autotuned_plan_matches_heuristic_plan():
     assert max(rel(lt[i], xs[i]) for i in range(len(probs))) <= LAMBDA_RTOL
     plan_c = _plan(probs)
     sc = sspcg.sspcg_plan_schedule(plan_c)
-    assert ([(g["block"], g["stream"], g["share"], g["tuned"]) for g in sc] ==
-            [(g["block"], g["stream"], g["share"], 1) for g in sched["pipeline"]])
+    assert ([(g["block"], g["stream"], g["share"], g["warps"], g["tuned"]) for g in sc] ==
+            [(g["block"], g["stream"], g["share"], g["warps"], 1) for g in sched["pipeline"]])
     sspcg.sspcg_autotune_cache_clear()
     assert not any(g["tuned"] for g in sspcg.sspcg_plan_schedule(_plan(probs)))
+
+
+@pytest.mark.parametrize("poly", [0, 1])
+def test_warp_schedule_matches_oracle(poly):
+    """Schedule "warp": every fully staged group runs one problem per warp, several problems per CTA (FP32
+    with double-float sums, and the FP64 path of the small problems); lambda and iterations against the oracle,
+    for the pipeline and for the PCG-only batched call on the pipeline's blocks."""
+    probs = P.make_workload(P.RAGGED_BATCH_4096, count=256)
+    probs += P.custom_problems([(0, 3, 2), (1, 1, 1), (5, 28, 14), (0, 1, 1), (12, 9, 0), (2, 17, 9)], config=63)
+    plan = _plan(probs, schedule="warp", poly_degree=poly)
+    sched = {w: sspcg.sspcg_plan_schedule(plan, w) for w in ("pipeline", "pipeline_f64", "solve_qp")}
+    for w in ("pipeline", "pipeline_f64"):
+        assert any(g["warps"] >= 2 for g in sched[w]), w
+    for g in sum(sched.values(), []):
+        if g["cls"] in (0, 5):
+            assert g["warps"] == 0
+        if g["warps"] > 0:
+            assert g["block"] == 32 * g["warps"] and g["smem"] % (16 * g["warps"]) == 0
+    b = sspcg.Batch(plan, probs)
+    b.pipeline("sym")
+    torch.cuda.synchronize()
+    xs, it_o, _, st_o, _, _ = block.solve_batch(probs, "sym", 1e-6, degree=poly)
+    assert (b.status.cpu().numpy() == 0).all() and (st_o == 0).all() and (b.relres.cpu().numpy() <= 1e-6).all()
+    it = b.iters.cpu().numpy()
+    lams = b.lambdas()
+    for i, p in enumerate(probs):
+        assert iters_match(it[i], it_o[i], p), (i, p.N, p.nx, it[i], it_o[i])
+    assert max(rel(lams[i], xs[i]) for i in range(len(probs))) <= LAMBDA_RTOL
+    # the PCG-only batched call on the same blocks
+    d = b.dev
+    lam2 = torch.zeros_like(b.lam); it2 = torch.zeros_like(b.iters); rr2 = torch.zeros_like(b.relres)
+    st2 = torch.zeros_like(b.status)
+    sspcg.sspcg_solve_qp_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE, d["gamma"], lam2, it2, rr2, st2)
+    torch.cuda.synchronize()
+    big = [i for i, p in enumerate(probs) if not is_tiny(p)]
+    assert (st2.cpu().numpy() == 0).all()
+    assert (it2.cpu().numpy()[big] == it[big]).all()
+    l2 = plan.unpack(sspcg.ARRAY_VEC, lam2, [p.gamma.shape for p in probs])
+    assert all(np.array_equal(l2[i], lams[i]) for i in big)
