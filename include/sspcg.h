@@ -511,7 +511,9 @@ sspcg_status sspcg_plan_join(sspcg_plan *plan, sspcg_stream stream);
  * returns without waiting for the GPU.
  *
  * Warm-up: the first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make it before any stream capture.  The first
+ * (cudaGetSymbolAddress); make it before any stream capture.  Later calls
+ * can be captured into a CUDA graph: they launch kernels only, so a replay
+ * solves the captured batch again (same shapes and pointers).  The first
  * launch of each PCG kernel variant (each nx and each reduction, schedule or
  * CG option) sets that kernel's shared-memory attribute and, under lazy
  * module loading, may load its code.  Callers with a time bound (a control

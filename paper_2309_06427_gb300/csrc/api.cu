@@ -260,6 +260,12 @@ struct sspcg_plan {
   int64_t *d_roff = nullptr;
   std::vector<NxGroup> nxg_r;
   bool full_ready = false;
+  // padded copies of A, B and PE for the problems whose block rows stream (QP form, FP32 sets): the PCG
+  // reads their streamed rows 16 bytes at a time (launch_pad_rows)
+  float *d_pad = nullptr;
+  int64_t *d_pad_off = nullptr;  // per problem: offset in d_pad, or -1
+  int32_t *d_pad_list = nullptr;  // the padded problems (indices into d_desc)
+  int32_t npad = 0;
 };
 
 namespace {
@@ -270,7 +276,7 @@ void plan_free(sspcg_plan *p) {
   for (void *ptr : {(void *)p->d_desc, (void *)p->d_kref, (void *)p->d_oref, (void *)p->d_knot_start, (void *)p->d_tdesc,
                     (void *)p->d_tkref, (void *)p->d_toref, (void *)p->D64, (void *)p->E64,
                     (void *)p->PD64, (void *)p->PE64, (void *)p->d_work, (void *)p->d_counters, (void *)p->d_scratch, (void *)p->hbuf,
-                    (void *)p->hint, (void *)p->hdbl})
+                    (void *)p->hint, (void *)p->hdbl, (void *)p->d_pad, (void *)p->d_pad_off, (void *)p->d_pad_list})
     cudaFree(ptr);
   for (auto *v : {&p->nxg_all, &p->nxg_tiny})
     for (NxGroup &g : *v) {
@@ -820,6 +826,29 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
     if ((e = cudaMemcpy(p->d_work, work.data(), sizeof(int32_t) * nwork, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e));
     {
+      // padded copies for the problems of the QP-form set that do not fit in shared memory whole (and, under
+      // the STREAM schedule, for every problem): N nx (2 vec_stride(nx) + vec_stride(nu)) floats each
+      std::vector<int64_t> off(nprob, -1);
+      std::vector<int32_t> list;
+      int64_t total = 0;
+      for (const PcgGroup &g : p->sets[kSetQpAll].groups) {
+        if (!(g.cls == 0 || g.cls == 5 || p->opts.schedule == SSPCG_SCHED_STREAM)) continue;
+        for (int32_t i : g.members) {
+          const ProbDesc &d = p->hdesc[i];
+          if (d.N == 0) continue;
+          off[d.id] = total;
+          list.push_back(i);
+          total += (int64_t)d.N * d.nx * (2 * vec_stride(d.nx) + vec_stride(d.nu));
+        }
+      }
+      p->npad = (int32_t)list.size();
+      if (p->npad > 0) {
+        if ((e = cudaMalloc(&p->d_pad, sizeof(float) * total)) != cudaSuccess) return fail(cuda_fail(e));
+        if ((e = upload(&p->d_pad_off, off)) != cudaSuccess) return fail(cuda_fail(e));
+        if ((e = upload(&p->d_pad_list, list)) != cudaSuccess) return fail(cuda_fail(e));
+      }
+    }
+    {
       // bytes: the largest set alone, or the pipeline's FP32 and FP64 sets side by side
       const int64_t b32 = (int64_t)sizeof(float), b64 = (int64_t)sizeof(double);
       auto sb = [&](int k) { return p->sets[k].scratch_elems * (p->sets[k].f64 ? b64 : b32); };
@@ -1007,6 +1036,18 @@ static PcgArgs batched_args(sspcg_plan *plan, const float *A, const float *B, co
   return a;
 }
 
+// Padded copies of the streamed problems' A, B and PE (PE nullptr: block-diagonal preconditioner, no copy), on
+// st before the PCG launches of a QP-form FP32 set, and the launch arguments that point the kernel at them.
+static sspcg_status pad_streamed(sspcg_plan *plan, const float *A, const float *B, const float *PE, PcgArgs &a,
+                                 cudaStream_t st) {
+  if (plan->npad == 0) return SSPCG_OK;
+  SSPCG_CUDA(launch_pad_rows(plan->d_desc, plan->d_pad_list, plan->npad, A, B, PE, plan->d_pad_off, plan->d_pad,
+                             device_sms(), st));
+  a.pad = plan->d_pad;
+  a.pad_off = plan->d_pad_off;
+  return SSPCG_OK;
+}
+
 static sspcg_status check_solve_args(sspcg_plan *plan, int op, const float *A, const float *B, const float *qd,
                                      const float *rd, const float *D, const float *E, const float *PD,
                                      const float *PE, const float *gamma, float *lambda, int32_t *iters,
@@ -1050,9 +1091,9 @@ sspcg_status sspcg_solve_qp_batched(sspcg_plan *plan, const float *A, const floa
   SSPCG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * plan->nprob, st));
   plan->build_timed = false;
   time_mark(plan, 1, st);
-  s = launch_sets(plan, {{&plan->sets[kSetQpAll], batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma,
-                                                               lambda, iters, relres, status)}},
-                  st);
+  PcgArgs a = batched_args(plan, A, B, qd, rd, nullptr, nullptr, PD, PE, gamma, lambda, iters, relres, status);
+  if ((s = pad_streamed(plan, A, B, PE, a, st)) != SSPCG_OK) return s;
+  s = launch_sets(plan, {{&plan->sets[kSetQpAll], a}}, st);
   time_mark(plan, 2, st);
   return s;
 }
@@ -1107,9 +1148,9 @@ static sspcg_status pipeline_solve(sspcg_plan *plan, const float *A, const float
   a64.ps = tiny_set(plan);
   a64.PD = plan->PD64;
   a64.PE = diag_only ? nullptr : plan->PE64;
-
-
-  sspcg_status s = launch_sets(plan, {{&plan->sets[kSetQpMain], a32}, {&plan->sets[kSetTiny], a64}}, st);
+  sspcg_status s = pad_streamed(plan, A, B, diag_only ? nullptr : PE, a32, st);
+  if (s != SSPCG_OK) return s;
+  s = launch_sets(plan, {{&plan->sets[kSetQpMain], a32}, {&plan->sets[kSetTiny], a64}}, st);
   time_mark(plan, 2, st);
   return s;
 }
@@ -1303,8 +1344,9 @@ sspcg_status sspcg_plan_autotune(sspcg_plan *plan, int32_t which, sspcg_precond 
     a64.ps = tiny_set(plan);
     a64.PD = plan->PD64;
     a64.PE = diag_only ? nullptr : plan->PE64;
+    s = pad_streamed(plan, A, B, diag_only ? nullptr : PE, a32, st);
 
-    if (which & SSPCG_TUNE_PIPELINE) {
+    if (s == SSPCG_OK && (which & SSPCG_TUNE_PIPELINE)) {
       s = tune_set(plan, plan->sets[kSetQpMain], plan->hdesc, a32, status0, st, e0, e1);
       if (s == SSPCG_OK) s = tune_set(plan, plan->sets[kSetTiny], plan->tdesc, a64, status0, st, e0, e1);
     }

@@ -124,7 +124,16 @@ struct PcgArgs {
   void *gscratch;        // vectors in global memory: CTA b uses gscratch + b * gstride elements
   int64_t gstride;       //   (nullptr: vectors in shared memory)
   int32_t warp;          // 1: one problem per warp (smem_elems per warp), QP form, textbook PCG
+  const float *pad;      // padded copies of A, B, PE of the streamed problems (QP form, FP32), or nullptr
+  const int64_t *pad_off;  // per problem id: offset of its copies in pad, or -1 (read the inputs)
 };
+
+// Padded copies for the streamed block rows of the listed problems (desc indices): A_k and PE_k rows of
+// vec_stride(nx) values, B_k rows of vec_stride(nu), zeros in the padding; problem p's copies start at
+// pad_off[desc[p].id] (A, then B at + N nx NXP, then PE at + N nx (NXP + NUP)).  PE nullptr: no PE copy.
+cudaError_t launch_pad_rows(const ProbDesc *desc, const int32_t *list, int32_t count, const float *A,
+                            const float *B, const float *PE, const int64_t *pad_off, float *pad, int sms,
+                            cudaStream_t st);
 
 // PCG launch for one nx; dispatches to the instantiation for that nx.
 // f64: the FP64 path (QP operator form only).  Each problem stages as many

@@ -153,6 +153,53 @@ __device__ __forceinline__ Real dot_seg(const MT *m, int stride, const Real *seg
   return a0 + a1;
 }
 
+// sum_{j < NX} m[j] * seg[j] for a 16-byte aligned row in global memory (the padded copies of streamed
+// block rows), read through the read-only path with 128-bit loads (four FP32 or two FP64 values; entries past
+// NX are padding and are not used); MT is the stored type.  The accumulation of dot_seg: even j into a0, odd
+// j into a1, each in increasing j, so the result is bit-identical.
+template <int NX, typename Real, typename MT>
+__device__ __forceinline__ Real dot_row_g(const MT *m, const Real *seg) {
+  constexpr int NXP = (NX + 3) & ~3;
+  Real a0 = Real(0), a1 = Real(0);
+#pragma unroll
+  for (int q = 0; q < NXP * (int)sizeof(MT) / 16; ++q) {
+    const float4 c = __ldg(reinterpret_cast<const float4 *>(m) + q);
+    if constexpr (sizeof(MT) == 4) {
+      const int j = 4 * q;
+      if (j < NX) a0 = rfma((Real)c.x, seg[j], a0);
+      if (j + 1 < NX) a1 = rfma((Real)c.y, seg[j + 1], a1);
+      if (j + 2 < NX) a0 = rfma((Real)c.z, seg[j + 2], a0);
+      if (j + 3 < NX) a1 = rfma((Real)c.w, seg[j + 3], a1);
+    } else {
+      const double2 dd = *reinterpret_cast<const double2 *>(&c);
+      const int j = 2 * q;
+      if (j < NX) a0 = rfma((Real)dd.x, seg[j], a0);
+      if (j + 1 < NX) a1 = rfma((Real)dd.y, seg[j + 1], a1);
+    }
+  }
+  return a0 + a1;
+}
+
+// Row (k, i) of the preconditioner for a streamed block row: PD dense (row stride NX, read by column), PE
+// with row stride ldo; pad: PE rows are 16-byte aligned (the padded copy) and its sub-diagonal row is read
+// with 128-bit loads.  The operation order of bt_row.
+template <int NX, typename Real>
+__device__ __forceinline__ Real bt_row_stream(const Real *Md, const Real *Mo, int ldo, bool pad, int N, int k, int i,
+                                              const Real *v) {
+  constexpr int NXP = (NX + 3) & ~3;
+  Seg<NX, Real> s0, s1, s2;
+  s0.load(v + k * NXP);
+  s1.load(v + (k - 1) * NXP);
+  s2.load(v + (k + 1) * NXP);
+  const int km = k > 0 ? k - 1 : 0;
+  const int kp = k < N ? k : (N > 0 ? N - 1 : 0);
+  const Real a = dot_seg<NX, false, Real>(Md + (int64_t)k * NX * NX + i, NX, s0.v);
+  const Real b = pad ? dot_row_g<NX, Real>(Mo + ((int64_t)km * NX + i) * ldo, s1.v)
+                     : dot_seg<NX, false, Real>(Mo + ((int64_t)km * NX + i) * ldo, 1, s1.v);
+  const Real c = dot_seg<NX, false, Real>(Mo + (int64_t)kp * NX * ldo + i, ldo, s2.v);
+  return (a + b) + c;
+}
+
 // Row (k, i) of a block-tridiagonal symmetric matrix times v (block-row
 // stride NXP): Md diagonal blocks (symmetric; read by column so that
 // consecutive i are consecutive addresses), Mo sub-diagonal blocks with
@@ -222,6 +269,8 @@ struct Views {
   const float *gA, *gB, *gD, *gE;                 // FP32 inputs (global)
   const Real *gPD, *gPE;                          // preconditioner (global)
   int ld, ldb;                                    // staged row strides
+  int gld, gldb;                                  // row strides of gA and gPE, and of gB, in global memory
+  bool gpad;                                      // gA, gB, gPE are the padded copies (16-byte aligned rows)
 };
 
 template <int NX, int OP, int RED, typename Real, bool CG = false, bool WARP = false>
@@ -276,6 +325,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   Views<Real> V{};
   V.ld = pad_ld(NX);
   V.ldb = pad_ld(nu > 0 ? nu : 1);
+  V.gld = NX; V.gldb = nu; V.gpad = false;
   V.gPD = reinterpret_cast<const Real *>(a.PD) + d.odiag;
   V.gPE = reinterpret_cast<const Real *>(a.PE) + d.ooff;
   {
@@ -307,6 +357,16 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       sir[k * NUP + j] = Real(1) / (Real)gr[e];
     }
     V.sA = s0; V.sB = s1;
+    // streamed block rows: the plan's padded copies of A, B and PE when it made them (rows of NXP, NUP
+    // values, 16-byte aligned, so that row-wise reads take 128-bit loads), else the inputs themselves
+    const int64_t po = (a.pad != nullptr && K < n) ? a.pad_off[p] : -1;
+    if (po >= 0) {
+      V.gpad = true;
+      V.gld = NXP; V.gldb = NUP;
+      V.gA = a.pad + po;
+      V.gB = a.pad + po + (int64_t)N * NX * NXP;
+      V.gPE = reinterpret_cast<const Real *>(a.pad + po + (int64_t)N * NX * (NXP + NUP));
+    }
   } else {
     V.gD = a.D + d.odiag;
     V.gE = a.E + d.ooff;
@@ -333,7 +393,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
           Seg<NX, Real> s;
           s.load(src + (k + 1) * NXP);
           const Real ax = k < K ? dot_seg<NX, true, Real>(V.sA + kp * NX * V.ld + j, V.ld, s.v)
-                                : dot_seg<NX, false, Real>(V.gA + (int64_t)kp * NX * NX + j, NX, s.v);
+                                : dot_seg<NX, false, Real>(V.gA + (int64_t)kp * NX * V.gld + j, V.gld, s.v);
           sv[k * NXP + j] = (-src[k * NXP + j] + ax) * siq[k * NXP + j];
         } else {
           const int t2 = it - R_;
@@ -343,7 +403,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
           s.load(src + (k + 1) * NXP);
           Real acc;
           if (k < K) acc = dot_seg<NX, true, Real>(V.sB + k * NX * V.ldb + j, V.ldb, s.v);
-          else acc = dot_seg<NX, false, Real>(V.gB + (int64_t)k * NX * nu + j, nu, s.v);
+          else acc = dot_seg<NX, false, Real>(V.gB + (int64_t)k * NX * V.gldb + j, V.gldb, s.v);
           svu[k * NUP + j] = acc * sir[k * NUP + j];
         }
       }
@@ -366,9 +426,20 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
         const Real *Br = V.sB + (km * NX + i) * V.ldb;
         for (int j = 0; j < nu; ++j) ab = rfma(Br[j], vu[j], ab);
       } else {
-        ax = dot_seg<NX, false, Real>(V.gA + ((int64_t)km * NX + i) * NX, 1, s.v);
-        const float *Br = V.gB + ((int64_t)km * NX + i) * nu;
-        for (int j = 0; j < nu; ++j) ab = rfma((Real)__ldg(Br + j), vu[j], ab);
+        const float *Br = V.gB + ((int64_t)km * NX + i) * V.gldb;
+        if (V.gpad) {  // padded rows: 128-bit loads
+          ax = dot_row_g<NX, Real>(V.gA + ((int64_t)km * NX + i) * V.gld, s.v);
+          for (int j4 = 0; j4 < nu; j4 += 4) {
+            const float4 bc = __ldg(reinterpret_cast<const float4 *>(Br + j4));
+            const float *bq = reinterpret_cast<const float *>(&bc);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (j4 + t < nu) ab = rfma((Real)bq[t], vu[j4 + t], ab);
+          }
+        } else {
+          ax = dot_seg<NX, false, Real>(V.gA + ((int64_t)km * NX + i) * NX, 1, s.v);
+          for (int j = 0; j < nu; ++j) ab = rfma((Real)__ldg(Br + j), vu[j], ab);
+        }
       }
       acc += ax;
       acc += ab;
@@ -386,7 +457,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
                    : dot_seg<NX, false, Real>(V.gPD + (int64_t)k * NX * NX + i, NX, s.v);
     }
     return k < K ? bt_row<NX, true, Real>(V.sPD, V.sPE, V.ld, N, k, i, src)
-                 : bt_row<NX, false, Real>(V.gPD, V.gPE, NX, N, k, i, src);
+                 : bt_row_stream<NX, Real>(V.gPD, V.gPE, V.gld, V.gpad, N, k, i, src);
   };
 
   // dst = Phi_d^-1 sr (polynomial of degree d = poly, Horner correction form as in ``precondition``); ends

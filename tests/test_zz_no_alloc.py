@@ -72,3 +72,45 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     with pytest.raises(sspcg.SspcgError, match="invalid argument"):
         sspcg.sspcg_solve_qp_batched_noalloc([4] * n, [2] * n, [1] * n, z, z, z, z, z, z, z, z,
                                              sspcg.options(), zi, zd, zi)
+
+
+def test_noalloc_call_replays_from_a_cuda_graph():
+    """After a first call (the warm-up the header asks for), the allocation-free solve can be captured into a
+    CUDA graph: it copies nothing from host memory (the shapes travel as a set-up kernel's parameters), so each
+    replay solves the captured batch again, bit-identical to the direct call."""
+    probs = _batch()
+    opts = sspcg.options(tol=1e-6)
+    Ns, nxs, nus = [p.N for p in probs], [p.nx for p in probs], [p.nu for p in probs]
+    plan = sspcg.sspcg_plan_create(Ns, nxs, nus, opts)
+    b = sspcg.Batch(plan, probs)
+    d = b.dev
+    sspcg.sspcg_build_schur_batched(plan, d["A"], d["B"], d["qd"], d["rd"], b.D, b.E)
+    st0 = torch.zeros(plan.nprob, dtype=torch.int32, device="cuda")
+    sspcg.sspcg_build_precond_batched(plan, "sym", b.D, b.E, b.PD, b.PE, st0)
+
+    def outputs():  # lambda prefilled with a finite sentinel: the padding between problems is never written
+        return (plan.empty(sspcg.ARRAY_VEC, fill=123.0),
+                torch.full((plan.nprob,), -7, dtype=torch.int32, device="cuda"),
+                torch.zeros(plan.nprob, dtype=torch.float64, device="cuda"),
+                torch.full((plan.nprob,), 9, dtype=torch.int32, device="cuda"))
+
+    def call(o):
+        sspcg.sspcg_solve_qp_batched_noalloc(Ns, nxs, nus, d["A"], d["B"], d["qd"], d["rd"], b.PD, b.PE,
+                                             d["gamma"], o[0], opts, o[1], o[2], o[3])
+
+    direct = outputs()
+    call(direct)  # also the warm-up
+    torch.cuda.synchronize()
+    assert (direct[3].cpu().numpy() == 0).all()
+    cap = outputs()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        call(cap)
+    torch.cuda.synchronize()
+    for rep in range(2):
+        cap[0].fill_(123.0); cap[1].fill_(-7); cap[3].fill_(9)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(cap[0], direct[0]), rep
+        assert torch.equal(cap[1], direct[1]) and torch.equal(cap[2], direct[2]), rep
+        assert (cap[3].cpu().numpy() == 0).all(), rep
