@@ -80,21 +80,68 @@ template <> struct Red<kRedF64, double> {
   static __device__ __forceinline__ double get(T v) { return v; }
 };
 
-// Block-wide sum of K accumulators: warp butterflies, one slot per warp,
-// one barrier, then every warp sums the slots in the same order, so all
-// threads hold bit-identical results.
+// Pieces of the reductions for every accumulator type: the sum of two partial sums (double-float: TwoSum,
+// exact in its high and low parts, and the same whichever operand comes first), and warp shuffles.
+__device__ __forceinline__ float red_add(float a, float b) { return a + b; }
+__device__ __forceinline__ double red_add(double a, double b) { return a + b; }
+__device__ __forceinline__ df red_add(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ float red_shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double red_shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df red_shfl_xor(df v, int o) { return df_shfl_xor(v, o); }
+__device__ __forceinline__ float red_shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double red_shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ df red_shfl(df v, int src) {
+  return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+// Xor butterfly over the 16 lanes of each half-warp.  The two lanes of a pair add the same two values, so
+// every lane of a half ends with the same sum.
+template <typename T>
+__device__ __forceinline__ T half_warp_sum(T v) {
+#pragma unroll
+  for (int o = 8; o; o >>= 1) v = red_add(v, red_shfl_xor(v, o));
+  return v;
+}
+
+// Warp sum of two accumulators with the work split between the half-warps (reduce-scatter): lanes 0-15 end
+// with the sum of a, lanes 16-31 with the sum of b, each half identical across its lanes.  The first step
+// trades across the halves (each lane sends the value its half does not keep), the other four run within a
+// half on one value.
+template <typename T>
+__device__ __forceinline__ T warp_sum_split(T a, T b) {
+  const bool hi = (threadIdx.x & 31) >= 16;
+  const T keep = hi ? b : a, give = hi ? a : b;
+  return half_warp_sum(red_add(keep, red_shfl_xor(give, 16)));
+}
+
+// Block-wide sum of K accumulators, every thread holding bit-identical results: warp sums, one slot per warp,
+// one barrier, then every warp sums the slots (at most 16: CTAs have at most 512 threads) in the same order.
+// Pairs of accumulators go through warp_sum_split, a single one through a full butterfly; the second stage
+// reads the slots into both halves of the warp (or one half per accumulator of a pair) and sums them over a
+// half-warp, then lanes 0 and 16 broadcast a pair's two sums.
 template <class R, int K>
 __device__ __forceinline__ void block_sum(typename R::T (&v)[K], typename R::T *slots) {
+  using T = typename R::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int h = lane >> 4, l16 = lane & 15;
+  constexpr int P = K / 2;  // pairs
 #pragma unroll
-  for (int e = 0; e < K; ++e) v[e] = R::sum(v[e]);
-  if (lane == 0) {
-#pragma unroll
-    for (int e = 0; e < K; ++e) slots[e * 32 + wid] = v[e];
+  for (int q = 0; q < P; ++q) {
+    const T w = warp_sum_split(v[2 * q], v[2 * q + 1]);
+    if (l16 == 0) slots[(2 * q + h) * 32 + wid] = w;
+  }
+  if constexpr (K % 2 == 1) {
+    const T w = R::sum(v[K - 1]);
+    if (lane == 0) slots[(K - 1) * 32 + wid] = w;
   }
   __syncthreads();
 #pragma unroll
-  for (int e = 0; e < K; ++e) v[e] = R::sum(lane < nw ? slots[e * 32 + lane] : R::zero());
+  for (int q = 0; q < P; ++q) {
+    const T w = half_warp_sum(l16 < nw ? slots[(2 * q + h) * 32 + l16] : R::zero());
+    v[2 * q] = red_shfl(w, 0);
+    v[2 * q + 1] = red_shfl(w, 16);
+  }
+  if constexpr (K % 2 == 1) v[K - 1] = half_warp_sum(l16 < nw ? slots[(K - 1) * 32 + l16] : R::zero());
 }
 
 // The thread group that solves one problem: the CTA, or one warp (WARP: several problems per CTA, one per
@@ -110,8 +157,14 @@ __device__ __forceinline__ void group_sync() {
 template <class R, int K, bool WARP>
 __device__ __forceinline__ void group_sum(typename R::T (&v)[K], typename R::T *slots) {
   if constexpr (WARP) {
+    constexpr int P = K / 2;
 #pragma unroll
-    for (int e = 0; e < K; ++e) v[e] = R::sum(v[e]);
+    for (int q = 0; q < P; ++q) {
+      const typename R::T w = warp_sum_split(v[2 * q], v[2 * q + 1]);
+      v[2 * q] = red_shfl(w, 0);
+      v[2 * q + 1] = red_shfl(w, 16);
+    }
+    if constexpr (K % 2 == 1) v[K - 1] = R::sum(v[K - 1]);
     __syncwarp();
   } else {
     block_sum<R, K>(v, slots);
