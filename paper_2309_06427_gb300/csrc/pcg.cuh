@@ -331,6 +331,7 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
   using R = Red<RED, Real>;
   using AccT = typename R::T;
   constexpr int NXP = (NX + 3) & ~3;
+  constexpr int NUC = (NX + 1) / 2;  // nu = ceil(nx / 2), the usual input count: unrolled B-row products
   const int p = d.id;  // output slot
   const int N = d.N, n = N + 1, nu = d.nu, R_ = n * NX, NUP = vec_stride(nu);
   const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x, T = WARP ? 32 : (int)blockDim.x;
@@ -477,10 +478,29 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       if (k < K) {
         ax = dot_seg<NX, true, Real>(V.sA + (km * NX + i) * V.ld, 1, s.v);
         const Real *Br = V.sB + (km * NX + i) * V.ldb;
-        for (int j = 0; j < nu; ++j) ab = rfma(Br[j], vu[j], ab);
+        if (nu == NUC) {  // unrolled, v_u in registers (128-bit loads)
+          Seg<NUC, Real> su_;
+          su_.load(vu);
+#pragma unroll
+          for (int j = 0; j < NUC; ++j) ab = rfma(Br[j], su_.v[j], ab);
+        } else {
+          for (int j = 0; j < nu; ++j) ab = rfma(Br[j], vu[j], ab);
+        }
       } else {
         const float *Br = V.gB + ((int64_t)km * NX + i) * V.gldb;
-        if (V.gpad) {  // padded rows: 128-bit loads
+        if (V.gpad && nu == NUC) {  // padded rows: 128-bit loads; unrolled, v_u in registers
+          ax = dot_row_g<NX, Real>(V.gA + ((int64_t)km * NX + i) * V.gld, s.v);
+          Seg<NUC, Real> su_;
+          su_.load(vu);
+#pragma unroll
+          for (int j4 = 0; j4 < NUC; j4 += 4) {
+            const float4 bc = __ldg(reinterpret_cast<const float4 *>(Br + j4));
+            const float *bq = reinterpret_cast<const float *>(&bc);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (j4 + t < NUC) ab = rfma((Real)bq[t], su_.v[j4 + t], ab);
+          }
+        } else if (V.gpad) {  // padded rows: 128-bit loads
           ax = dot_row_g<NX, Real>(V.gA + ((int64_t)km * NX + i) * V.gld, s.v);
           for (int j4 = 0; j4 < nu; j4 += 4) {
             const float4 bc = __ldg(reinterpret_cast<const float4 *>(Br + j4));
