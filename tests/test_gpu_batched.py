@@ -282,3 +282,34 @@ def test_warp_schedule_matches_oracle(poly):
     assert (it2.cpu().numpy()[big] == it[big]).all()
     l2 = plan.unpack(sspcg.ARRAY_VEC, lam2, [p.gamma.shape for p in probs])
     assert all(np.array_equal(l2[i], lams[i]) for i in big)
+
+
+@pytest.mark.parametrize("schedule", ["auto", "stream"])
+def test_streamed_problems_with_other_input_counts(schedule):
+    """Problems too large for shared memory whose input count nu is not ceil(nx/2) (the B-row products then
+    take the general loop, on the padded copies of the streamed rows): lambda and iterations against the
+    oracle, for the batched pipeline and for the single-problem path, which reads the unpadded inputs."""
+    probs = P.custom_problems([(200, 21, 5), (160, 14, 0), (180, 12, 12), (90, 28, 3), (120, 21, 11)], config=67)
+    plan = _plan(probs, schedule=schedule)
+    assert sspcg.plan_stats(plan)["solve_qp_stream"] >= 4
+    b = sspcg.Batch(plan, probs)
+    b.pipeline("sym")
+    torch.cuda.synchronize()
+    xs, it_o, _, st_o, _, _ = block.solve_batch(probs, "sym", 1e-6)
+    assert (b.status.cpu().numpy() == 0).all() and (st_o == 0).all()
+    it = b.iters.cpu().numpy()
+    lams = b.lambdas()
+    # FP32 iteration counts of inputless dynamics (nu = 0, kappa(Phi_sym^-1 S) ~ 3e3) are not compared with
+    # the FP64 oracle's: lambda and convergence only
+    for i, p in enumerate(probs):
+        if p.nu > 0:
+            assert iters_match(it[i], it_o[i], p), (i, p.N, p.nx, p.nu, it[i], it_o[i])
+        assert rel(lams[i], xs[i]) <= LAMBDA_RTOL, (i, rel(lams[i], xs[i]))
+    assert (b.relres.cpu().numpy() <= 1e-6).all()
+    for i, p in enumerate(probs):
+        # the single-problem path (its own launch shape, so its sums run in another order) meets the same bar
+        lam1, it1, rr1, st1 = gpu_solve_auto(p, "sym", 1e-6, schedule=schedule)
+        assert st1 == 0 and rr1 <= 1e-6, (i, st1, rr1)
+        if p.nu > 0:
+            assert iters_match(it1, it_o[i], p), (i, it1, it_o[i])
+        assert rel(lam1, xs[i]) <= LAMBDA_RTOL, (i, rel(lam1, xs[i]))
