@@ -58,6 +58,13 @@ def test_invalid_shapes_rejected_on_host(L):
         bad = sspcg.options(poly_degree=deg)
         assert L.sspcg_solve(4, 4, vp, vp, vp, vp, vp, vp, ctypes.byref(bad), vp, vp, vp, None) == \
             sspcg.ERR_INVALID_ARG
+    # schedules: auto, resident, stream, warp (one problem per warp); anything else is rejected
+    assert sspcg.SCHED == {"auto": 0, "resident": 1, "stream": 2, "warp": 3}
+    for sched in (-1, 4):
+        bad = sspcg.options()
+        bad.schedule = sched
+        assert L.sspcg_solve(4, 4, vp, vp, vp, vp, vp, vp, ctypes.byref(bad), vp, vp, vp, None) == \
+            sspcg.ERR_INVALID_ARG
     # single-reduction PCG: variant 0 or 1, double-float sums (polynomial preconditioners are allowed)
     for bad in (sspcg.options(cg_variant=2), sspcg.options(cg_variant=1, reduction="f32")):
         assert L.sspcg_solve(4, 4, vp, vp, vp, vp, vp, vp, ctypes.byref(bad), vp, vp, vp, None) == \
