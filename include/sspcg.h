@@ -263,7 +263,12 @@ sspcg_status sspcg_residual_qp(int32_t N, int32_t nx, int32_t nu, const float *A
  * one device buffer per array kind, each problem starting at a 16-byte
  * aligned offset given by sspcg_plan_offsets.  The plan owns its device
  * descriptors and work lists (allocated here, freed by sspcg_plan_destroy)
- * and picks a kernel schedule per problem class.
+ * and picks a kernel schedule per problem class.  It also holds padded
+ * copies of A, B and PE for the problems that do not fit in shared memory
+ * whole (every problem under SSPCG_SCHED_STREAM): N nx (2 nx4 + nu4) floats
+ * each, with nx4 and nu4 rounded up to multiples of 4.  The QP-form batched
+ * solves rewrite them from their arguments on every call, and the PCG reads
+ * the streamed block rows from them with 128-bit loads.
  * N, nx, nu: host arrays of nprob entries.  opts: host pointer, copied.
  */
 typedef struct sspcg_plan sspcg_plan;
@@ -398,10 +403,12 @@ sspcg_status sspcg_plan_launch(sspcg_plan *plan, sspcg_stream stream);
  * sets (which: SSPCG_TUNE_PIPELINE, the pipeline's FP32 and FP64 sets;
  * SSPCG_TUNE_SOLVE, the set of sspcg_solve_qp_batched; or both; one group
  * per nx and residency class), times candidate schedules alone on these
- * inputs: block sizes 64..512 threads (16 rows per thread to one) and,
- * for groups that do not fit in shared memory whole, staging the first rows
- * into the whole budget or into 1/2, 1/3 or 1/4 of it (several CTAs per
- * SM), or streaming every block row from L2.  Each group keeps its fastest
+ * inputs: block sizes 64..512 threads (16 rows per thread to one); for
+ * groups that do not fit in shared memory whole, staging the first rows into
+ * the whole budget or into 1/2, 1/3 or 1/4 of it (several CTAs per SM), or
+ * streaming every block row from L2; for groups that do fit (QP form,
+ * textbook PCG, double-float or FP64 sums), also one problem per warp with
+ * 1 to 16 warps per CTA.  Each group keeps its fastest
  * candidate (grid from the kernel's occupancy at that block size); the
  * choices also go to a process-wide cache keyed by (launch set, operator form,
  * precision, reduction, polynomial degree, PCG variant, nx, residency class,
