@@ -265,7 +265,7 @@ sspcg_status sspcg_residual_qp(int32_t N, int32_t nx, int32_t nu, const float *A
  * descriptors and work lists (allocated here, freed by sspcg_plan_destroy)
  * and picks a kernel schedule per problem class.  It also holds padded
  * copies of A, B and PE for the problems that do not fit in shared memory
- * whole (every problem under SSPCG_SCHED_STREAM): N nx (2 nx4 + nu4) floats
+ * whole (every problem under SSPCG_SCHED_STREAM): about N nx (2 nx4 + nu4) floats
  * each, with nx4 and nu4 rounded up to multiples of 4.  The QP-form batched
  * solves rewrite them from their arguments on every call, and the PCG reads
  * the streamed block rows from them with 128-bit loads.

@@ -838,7 +838,8 @@ sspcg_status sspcg_plan_create(sspcg_plan **plan, int32_t nprob, const int32_t *
           if (d.N == 0) continue;
           off[d.id] = total;
           list.push_back(i);
-          total += (int64_t)d.N * d.nx * (2 * vec_stride(d.nx) + vec_stride(d.nu));
+          const int64_t rows = (int64_t)d.N * d.nx;
+          total += 2 * pad_region(rows, d.nx) + pad_region(rows, d.nu);  // multiples of 8 floats
         }
       }
       p->npad = (int32_t)list.size();

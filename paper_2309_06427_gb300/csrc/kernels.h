@@ -128,9 +128,16 @@ struct PcgArgs {
   const int64_t *pad_off;  // per problem id: offset of its copies in pad, or -1 (read the inputs)
 };
 
+// Floats of one padded region (rows of vec_stride(width) values), a multiple of 8 so that every region of a
+// problem starts 32-byte aligned (the PCG reads padded rows of a multiple of 8 values with 256-bit loads).
+__host__ __device__ __forceinline__ int64_t pad_region(int64_t rows, int width) {
+  return round_up(rows * vec_stride(width), 8);
+}
+
 // Padded copies for the streamed block rows of the listed problems (desc indices): A_k and PE_k rows of
 // vec_stride(nx) values, B_k rows of vec_stride(nu), zeros in the padding; problem p's copies start at
-// pad_off[desc[p].id] (A, then B at + N nx NXP, then PE at + N nx (NXP + NUP)).  PE nullptr: no PE copy.
+// pad_off[desc[p].id] (a multiple of 8 floats): A, then B at + pad_region(N nx, nx), then PE after B's
+// pad_region(N nx, nu).  PE nullptr: no PE copy.
 cudaError_t launch_pad_rows(const ProbDesc *desc, const int32_t *list, int32_t count, const float *A,
                             const float *B, const float *PE, const int64_t *pad_off, float *pad, int sms,
                             cudaStream_t st);

@@ -52,8 +52,9 @@ __global__ void __launch_bounds__(kPadThreads) pad_rows_kernel(const ProbDesc *d
     const int nxp = vec_stride(d.nx), nup = vec_stride(d.nu);
     const int rows = d.N * d.nx;
     pad_block_rows(pad + po, A + d.oA, rows, d.nx, nxp);
-    if (d.nu > 0) pad_block_rows(pad + po + (int64_t)rows * nxp, B + d.oB, rows, d.nu, nup);
-    if (PE) pad_block_rows(pad + po + (int64_t)rows * (nxp + nup), PE + d.ooff, rows, d.nx, nxp);
+    const int64_t ra = pad_region(rows, d.nx), rb = pad_region(rows, d.nu);
+    if (d.nu > 0) pad_block_rows(pad + po + ra, B + d.oB, rows, d.nu, nup);
+    if (PE) pad_block_rows(pad + po + ra + rb, PE + d.ooff, rows, d.nx, nxp);
   }
 }
 

@@ -214,6 +214,26 @@ template <int NX, typename Real, typename MT>
 __device__ __forceinline__ Real dot_row_g(const MT *m, const Real *seg) {
   constexpr int NXP = (NX + 3) & ~3;
   Real a0 = Real(0), a1 = Real(0);
+  if constexpr (sizeof(MT) == 4 && NXP % 8 == 0) {
+    // padded FP32 rows of a multiple of 8 values start 32-byte aligned (pad_region): 256-bit loads
+#pragma unroll
+    for (int q = 0; q < NXP / 8; ++q) {
+      float c[8];
+      asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                   : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]),
+                     "=f"(c[7])
+                   : "l"(m + 8 * q));
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int j = 8 * q + t;
+        if (j < NX) {
+          if (t % 2 == 0) a0 = rfma((Real)c[t], seg[j], a0);
+          else a1 = rfma((Real)c[t], seg[j], a1);
+        }
+      }
+    }
+    return a0 + a1;
+  }
 #pragma unroll
   for (int q = 0; q < NXP * (int)sizeof(MT) / 16; ++q) {
     const float4 c = __ldg(reinterpret_cast<const float4 *>(m) + q);
@@ -418,8 +438,9 @@ __device__ void pcg_solve(const PcgArgs &a, const ProbDesc &d, Real *sm, typenam
       V.gpad = true;
       V.gld = NXP; V.gldb = NUP;
       V.gA = a.pad + po;
-      V.gB = a.pad + po + (int64_t)N * NX * NXP;
-      V.gPE = reinterpret_cast<const Real *>(a.pad + po + (int64_t)N * NX * (NXP + NUP));
+      V.gB = a.pad + po + pad_region((int64_t)N * NX, NX);
+      V.gPE = reinterpret_cast<const Real *>(a.pad + po + pad_region((int64_t)N * NX, NX) +
+                                             pad_region((int64_t)N * NX, nu));
     }
   } else {
     V.gD = a.D + d.odiag;
